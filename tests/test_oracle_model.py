@@ -1,0 +1,406 @@
+"""Pins of the oracle's rollout (Sec. III, IV-B, IV-D, V-D) against closed forms,
+an independent high-order ODE solver, brute-force fixed points, invariants and
+degenerate cases.  None of these re-runs the oracle's own formulas."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+from scipy.optimize import brentq
+
+import aeb_inputs as ai
+
+
+def one(params_rows):
+    """Build parameter columns from (v0, d0, mu, grade, mass, cd, tau, delay, noise) rows."""
+    a = np.array(params_rows, dtype=np.float64).reshape(-1, 9)
+    g = 9.81
+    return {"v0": a[:, 0].copy(), "d0": a[:, 1].copy(), "mu": a[:, 2].copy(),
+            "gs": g * np.sin(a[:, 3]), "gc": g * np.cos(a[:, 3]), "mass": a[:, 4].copy(),
+            "cd": a[:, 5].copy(), "tau": a[:, 6].copy(), "t_delay": a[:, 7].copy(),
+            "noise": a[:, 8].copy()}
+
+
+# ---------------------------------------------------------------------------
+# Constant deceleration: both axles at their limit (a_cmd = -15), no drag,
+# flat road, instantaneous actuator.  D = v0 t_b + v0^2 / (2 mu g).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("v0,mu,delay", [(15.0, 0.4, 0.1), (35.0, 0.9, 0.3), (27.3, 0.65, 0.0),
+                                         (20.0, 0.5, 0.2137)])
+def test_constant_deceleration_closed_form(oracle_mod, v0, mu, delay):
+    m = ai.Model(a_cmd=-15.0, lead=0)
+    p = one([(v0, 0.0, mu, 0.0, 1500.0, 0.0, 0.0, delay, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    r = mu * m.g
+    n_b = math.ceil(delay / m.dt - 1e-9)
+    t_b = n_b * m.dt
+    D = v0 * t_b + v0 * v0 / (2.0 * r)
+    assert o["status"][0] == 0
+    # linear refinement inside the last step misses the parabola by <= r dt^2 / 8
+    assert abs(o["x_ref"][0] - D) <= r * m.dt ** 2 / 8 + 1e-9
+    # the paper's raw D_stop = x(t_{n+1}) lies within r dt^2 / 2 below D
+    assert -r * m.dt ** 2 / 2 - 1e-9 <= o["x_raw"][0] - D <= 1e-9
+    assert abs(o["t_end"][0] - (t_b + v0 / r)) < 1e-9
+    # the closed form with the continuous delay holds up to onset quantisation
+    D_cont = v0 * delay + v0 * v0 / (2.0 * r)
+    assert abs(o["x_ref"][0] - D_cont) <= v0 * m.dt + r * m.dt ** 2
+
+
+def test_unsaturated_constant_deceleration(oracle_mod):
+    """Demand below both axle limits: the realised deceleration is the demand."""
+    m = ai.Model(a_cmd=-3.0, lead=0)
+    p = one([(25.0, 0.0, 0.9, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    assert abs(o["x_ref"][0] - 25.0 ** 2 / 6.0) <= 3.0 * m.dt ** 2 / 8 + 1e-9
+
+
+def test_lumped_cap_closed_form(oracle_mod):
+    """Eq. 5 as printed: r = min(|a_cmd|, mu g / (1 + mu h / L))."""
+    m = ai.paper_model()
+    for mu in (0.4, 0.6, 0.8, 1.0):
+        p = one([(30.0, 0.0, mu, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)])
+        o = oracle_mod.rollout(m, p)
+        r = min(6.0, mu * 9.81 / (1.0 + mu * 0.5 / 2.7))
+        assert abs(o["x_ref"][0] - 900.0 / (2 * r)) <= r * m.dt ** 2 / 8 + 1e-9
+
+
+@pytest.mark.parametrize("theta", [-0.08, -0.02, 0.03, 0.1])
+def test_grade_closed_form(oracle_mod, theta):
+    """Saturated axles on a grade: deceleration mu g cos(theta) + g sin(theta)."""
+    m = ai.Model(a_cmd=-15.0, lead=0)
+    p = one([(30.0, 0.0, 0.7, theta, 1500.0, 0.0, 0.0, 0.0, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    c = 0.7 * 9.81 * math.cos(theta) + 9.81 * math.sin(theta)
+    assert abs(o["x_ref"][0] - 900.0 / (2 * c)) <= c * m.dt ** 2 / 8 + 1e-9
+
+
+@pytest.mark.parametrize("v0,mu,mass", [(35.0, 0.9, 200.0), (20.0, 0.4, 300.0), (30.0, 0.7, 1600.0)])
+def test_quadratic_drag_closed_form(oracle_mod, v0, mu, mass):
+    """dv/dt = -c - k v^2: t_s = atan(v0 sqrt(k/c)) / sqrt(k c),
+    D = ln(1 + k v0^2 / c) / (2 k)."""
+    m = ai.Model(a_cmd=-15.0, lead=0)
+    cd = 0.35
+    p = one([(v0, 0.0, mu, 0.0, mass, cd, 0.0, 0.0, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    k = 1.225 * cd * 2.2 / (2 * mass)
+    c = mu * 9.81
+    D = math.log1p(k * v0 * v0 / c) / (2 * k)
+    ts = math.atan(v0 * math.sqrt(k / c)) / math.sqrt(k * c)
+    assert abs(o["x_ref"][0] - D) <= c * m.dt ** 2 / 8 + 1e-8
+    assert abs(o["t_end"][0] - ts) <= 1e-8
+
+
+@pytest.mark.parametrize("tau,delay", [(0.1, 0.0), (0.3, 0.0), (0.15, 0.2), (0.25, 0.123)])
+def test_actuator_lag_closed_form(oracle_mod, tau, delay):
+    """No drag, flat road, unsaturated demand a_c: after onset t_b,
+    v = v0 + a_c (s - tau (1 - e^{-s/tau})), x = v0 t_b + v0 s
+    + a_c (s^2/2 - tau s + tau^2 (1 - e^{-s/tau})), s = t - t_b."""
+    ac = -3.0
+    m = ai.Model(a_cmd=ac, lead=0)
+    v0 = 22.0
+    p = one([(v0, 0.0, 0.9, 0.0, 1500.0, 0.0, tau, delay, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    tb = math.ceil(delay / m.dt - 1e-9) * m.dt
+    v = lambda s: v0 + ac * (s - tau * (1 - math.exp(-s / tau)))
+    x = lambda s: v0 * tb + v0 * s + ac * (s * s / 2 - tau * s + tau * tau * (1 - math.exp(-s / tau)))
+    s_stop = brentq(v, 0.0, 60.0, xtol=1e-15)
+    assert abs(o["x_ref"][0] - x(s_stop)) <= 3.0 * m.dt ** 2 / 8 + 1e-8
+    assert abs(o["t_end"][0] - (tb + s_stop)) <= 1e-8
+
+
+def _dop853_state(v0, tau, ac, k, gs, T):
+    def f(t, y):
+        x, v, a = y
+        return [v, a - k * v * v - gs, (ac - a) / tau]
+    sol = solve_ivp(f, (0.0, T), [0.0, v0, 0.0], method="DOP853", rtol=1e-13, atol=1e-13)
+    return sol.y[0, -1], sol.y[1, -1]
+
+
+def test_rk4_fourth_order_convergence(oracle_mod):
+    """Smooth case (lag + drag + grade, demand below the axle limits, run to the
+    horizon): the error against DOP853 falls by ~2^4 per halving of dt."""
+    v0, tau, ac, mass, cd, theta, T = 30.0, 0.4, -2.0, 1500.0, 0.3, 0.02, 2.0
+    k = 1.225 * cd * 2.2 / (2 * mass)
+    gs = 9.81 * math.sin(theta)
+    x_ref, _ = _dop853_state(v0, tau, ac, k, gs, T)
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        m = ai.Model(a_cmd=ac, lead=0, dt=dt, t_max=T)
+        p = one([(v0, 0.0, 0.9, theta, mass, cd, tau, 0.0, 0.0)])
+        o = oracle_mod.rollout(m, p)
+        assert o["status"][0] == 2  # horizon
+        errs.append(abs(o["x_ref"][0] - x_ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 12.0 < r1 < 20.0 and 12.0 < r2 < 20.0, errs
+    m = ai.Model(a_cmd=ac, lead=0, dt=1e-3, t_max=T)
+    o = oracle_mod.rollout(m, one([(v0, 0.0, 0.9, theta, mass, cd, tau, 0.0, 0.0)]))
+    assert abs(o["x_ref"][0] - x_ref) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Contact with a stationary lead at d0
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d0,delay", [(40.0, 0.2), (55.5, 0.05), (3.0, 0.3)])
+def test_contact_kinematics(oracle_mod, d0, delay):
+    v0, mu = 30.0, 0.6
+    m = ai.Model(a_cmd=-15.0, lead=1)
+    p = one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    r = mu * 9.81
+    tb = math.ceil(delay / m.dt - 1e-9) * m.dt
+    assert o["status"][0] == 1
+    assert o["x_ref"][0] == d0
+    if d0 <= v0 * tb:
+        vi, tc = v0, d0 / v0
+    else:
+        rem = d0 - v0 * tb
+        vi = math.sqrt(v0 * v0 - 2 * r * rem)
+        tc = tb + (v0 - vi) / r
+    assert abs(o["v_imp"][0] - vi) <= 1e-5
+    assert abs(o["t_end"][0] - tc) <= 1e-6
+    assert o["x_raw"][0] >= d0
+
+
+def test_contact_wins_over_stop(oracle_mod):
+    """A car that would stop exactly past the lead makes contact (contact is
+    tested first), one that stops short does not."""
+    v0, mu = 20.0, 0.5
+    r = mu * 9.81
+    D = v0 * v0 / (2 * r)
+    m = ai.Model(a_cmd=-15.0, lead=1)
+    o = oracle_mod.rollout(m, one([(v0, D - 0.01, mu, 0, 1500, 0, 0, 0, 0),
+                                   (v0, D + 0.01, mu, 0, 1500, 0, 0, 0, 0),
+                                   (v0, D - 0.0005, mu, 0, 1500, 0, 0, 0, 0),
+                                   (v0, D + 0.0005, mu, 0, 1500, 0, 0, 0, 0)]))
+    assert list(o["status"]) == [1, 0, 1, 0]
+    assert o["v_imp"][0] > 0 and o["v_imp"][0] < math.sqrt(2 * r * 0.011)
+    assert o["v_imp"][2] > 0 and o["v_imp"][2] < math.sqrt(2 * r * 0.0006)
+    # contact is flagged in the step that first reaches the lead
+    for i in (0, 2):
+        assert 0.0 <= o["x_raw"][i] - o["x_ref"][i] <= o["v_imp"][i] * m.dt + 1e-9
+
+
+def test_ttc_trigger_step(oracle_mod):
+    """Coasting at constant speed (no drag, flat), the trigger fires at the first
+    step n with d0 - n v0 dt + noise <= thr v0; braking starts n_delay later."""
+    v0, mu, thr, noise, delay = 20.0, 0.8, 1.5, 0.37, 0.15
+    dt = 1e-3
+    d0 = 80.0
+    m = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=thr)
+    o = oracle_mod.rollout(m, one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, noise)]))
+    q = (d0 + noise - thr * v0) / (v0 * dt)       # 2518.5: far from an integer
+    assert abs(q - round(q)) > 0.1
+    n_t = math.ceil(q)
+    n_b = n_t + math.ceil(delay / dt - 1e-9)
+    x_b = v0 * n_b * dt
+    r = mu * 9.81
+    D = x_b + v0 * v0 / (2 * r)
+    assert D < d0
+    assert o["status"][0] == 0
+    assert abs(o["x_ref"][0] - D) <= r * dt * dt / 8 + 1e-8
+    # a positive range bias makes the measured gap larger, so without it the
+    # trigger fires earlier and the car stops shorter
+    o2 = oracle_mod.rollout(m, one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, 0.0)]))
+    assert o2["x_ref"][0] < o["x_ref"][0]
+    # a threshold that never fires: no braking, coast into the lead at v0
+    m0 = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=-1.0)
+    o3 = oracle_mod.rollout(m0, one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, 0.0)]))
+    assert o3["status"][0] == 1 and abs(o3["v_imp"][0] - v0) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Realised deceleration: brute-force fixed point of the force balance
+# ---------------------------------------------------------------------------
+
+def brute_per_axle(D, mu, gc, beta, phi, hl):
+    r = 0.0
+    for _ in range(400):
+        r_new = min(beta * D, mu * (gc * phi + r * hl)) + \
+            min((1 - beta) * D, mu * (gc * (1 - phi) - r * hl))
+        if abs(r_new - r) <= 1e-16 * max(1.0, abs(r)):
+            r = r_new
+            break
+        r = r_new
+    return r
+
+
+def brute_lumped(D, mu, g, hl):
+    r = 0.0
+    for _ in range(400):
+        r = min(D, mu * g - mu * hl * r)
+    return r
+
+
+def test_per_axle_cap_against_fixed_point(oracle_mod):
+    rng = np.random.default_rng(7)
+    for _ in range(3000):
+        mu = rng.uniform(0.0, 1.2)
+        theta = rng.normal(0.0, 0.1)
+        gc = 9.81 * math.cos(theta)
+        beta = rng.uniform(0.3, 0.9)
+        phi = rng.uniform(0.4, 0.7)
+        h, L = rng.uniform(0.3, 0.8), rng.uniform(2.3, 3.2)
+        D = rng.uniform(0.0, 20.0)
+        m = ai.Model(beta=beta, phi_f=phi, h_cg=h, wheelbase=L)
+        got = oracle_mod.axle_cap(m, mu, gc, D)
+        exp = brute_per_axle(D, mu, gc, beta, phi, h / L)
+        assert abs(got - exp) <= 1e-12 * max(1.0, exp), (mu, theta, beta, phi, h, L, D)
+
+
+def test_per_axle_special_cases(oracle_mod):
+    g = 9.81
+    # no weight transfer and the brake split matching the load split: min(D, mu g)
+    m = ai.Model(h_cg=0.0, beta=0.6, phi_f=0.6)
+    for D in (1.0, 5.0, 7.0, 12.0):
+        assert abs(oracle_mod.axle_cap(m, 0.7, g, D) - min(D, 0.7 * g)) < 1e-14
+    # a large demand saturates both axles: mu g cos(theta)
+    m = ai.Model()
+    assert abs(oracle_mod.axle_cap(m, 0.8, g * math.cos(0.05), 100.0) - 0.8 * g * math.cos(0.05)) < 1e-13
+    # a small demand is met in full
+    assert oracle_mod.axle_cap(m, 0.8, g, 0.5) == 0.5
+
+
+def test_lumped_cap_against_fixed_point(oracle_mod):
+    rng = np.random.default_rng(8)
+    for _ in range(500):
+        mu, D = rng.uniform(0.0, 1.2), rng.uniform(0.0, 15.0)
+        m = ai.Model(cap_mode=0, h_cg=0.5, wheelbase=2.7)
+        got = oracle_mod.axle_cap(m, mu, 9.81, D)
+        assert abs(got - brute_lumped(D, mu, 9.81, 0.5 / 2.7)) <= 1e-12 * max(1.0, got)
+
+
+def _active_piece(D, mu, gc, beta, phi, hl):
+    lines = [D, (mu * gc * phi + (1 - beta) * D) / (1 - mu * hl),
+             (beta * D + mu * gc * (1 - phi)) / (1 + mu * hl), mu * gc]
+    return int(np.argmin(lines))
+
+
+@pytest.mark.parametrize("beta,mu,acmd", [
+    (0.6, 0.9, -3.0),    # demand met
+    (0.95, 0.6, -6.0),   # front axle at its limit
+    (0.3, 0.6, -6.0),    # rear axle at its limit
+    (0.7, 0.5, -15.0),   # both axles at their limits
+])
+def test_rollout_with_each_axle_piece_active(oracle_mod, beta, mu, acmd):
+    """Instantaneous actuator, no drag, flat road: the realised deceleration is
+    the brute-force fixed point r, so D = v0^2 / (2 r); each case makes a
+    different piece of the force balance the active one."""
+    g, v0 = 9.81, 28.0
+    m = ai.Model(a_cmd=acmd, lead=0, beta=beta)
+    hl = m.h_cg / m.wheelbase
+    r = brute_per_axle(-acmd, mu, g, beta, m.phi_f, hl)
+    assert abs(r - oracle_mod.axle_cap(m, mu, g, -acmd)) < 1e-12
+    o = oracle_mod.rollout(m, one([(v0, 0.0, mu, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)]))
+    assert abs(o["x_ref"][0] - v0 * v0 / (2 * r)) <= r * m.dt ** 2 / 8 + 1e-9
+
+
+def test_each_axle_piece_is_exercised():
+    g, hl, phi = 9.81, 0.55 / 2.7, 0.6
+    pieces = {_active_piece(-a, mu, g, b, phi, hl)
+              for b, mu, a in ((0.6, 0.9, -3.0), (0.95, 0.6, -6.0), (0.3, 0.6, -6.0), (0.7, 0.5, -15.0))}
+    assert pieces == {0, 1, 2, 3}
+
+
+def test_ttc_trigger_step_random(oracle_mod):
+    """Random thresholds, gaps and range biases: the oracle's trigger step must be
+    the first n with d0 - n v0 dt + noise <= thr v0 (coasting at constant speed),
+    which fixes the stopping point to D = v0 (n_t + n_delay) dt + v0^2 / (2 mu g)."""
+    rng = np.random.default_rng(21)
+    dt, mu, v0 = 1e-3, 0.8, 20.0
+    r = mu * 9.81
+    rows, expect = [], []
+    while len(rows) < 60:
+        thr, noise, d0 = rng.uniform(1.5, 4.0), rng.normal(0, 0.5), rng.uniform(60, 120)
+        delay = rng.uniform(0.0, 0.3)
+        q = (d0 + noise - thr * v0) / (v0 * dt)
+        nd = math.ceil(delay / dt - 1e-9)
+        if abs(q - round(q)) < 1e-3 or abs(delay / dt - round(delay / dt)) < 1e-3 or q < 0:
+            continue
+        D = v0 * (math.ceil(q) + nd) * dt + v0 * v0 / (2 * r)
+        if D > d0 - 0.5:
+            continue
+        rows.append((v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, noise, thr))
+        expect.append(D)
+    for row, D in zip(rows, expect):
+        m = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=row[9])
+        o = oracle_mod.rollout(m, one([row[:9]]))
+        assert o["status"][0] == 0
+        assert abs(o["x_ref"][0] - D) <= r * dt * dt / 8 + 1e-8, (row, D, o["x_ref"][0])
+
+
+# ---------------------------------------------------------------------------
+# Monotonicity of the stopping distance along one-parameter sweeps
+# ---------------------------------------------------------------------------
+
+BASE = dict(v0=25.0, d0=0.0, mu=0.6, grade=0.0, mass=1600.0, cd=0.3, tau=0.2, delay=0.2, noise=0.0)
+ORDER = ("v0", "d0", "mu", "grade", "mass", "cd", "tau", "delay", "noise")
+
+
+@pytest.mark.parametrize("name,values,sign", [
+    ("v0", np.linspace(5, 40, 36), +1),
+    ("mu", np.linspace(0.1, 1.0, 37), -1),
+    ("grade", np.linspace(-0.1, 0.1, 41), -1),
+    ("mass", np.linspace(800, 3000, 23), +1),
+    ("cd", np.linspace(0.0, 0.8, 17), -1),
+    ("tau", np.linspace(0.0, 0.5, 26), +1),
+    ("delay", np.linspace(0.0, 0.6, 61), +1),
+])
+def test_monotone_sweeps(oracle_mod, name, values, sign):
+    rows = []
+    for val in values:
+        row = dict(BASE)
+        row[name] = val
+        rows.append(tuple(row[k] for k in ORDER))
+    m = ai.Model(lead=0)
+    d = oracle_mod.rollout(m, one(rows))["x_ref"]
+    steps = np.diff(d) * sign
+    assert np.all(steps >= -1e-9), (name, d)
+    assert d[-1] * sign > d[0] * sign
+
+
+def test_harder_braking_is_shorter(oracle_mod):
+    p = one([(25.0, 0.0, 0.9, 0.0, 1600, 0.3, 0.2, 0.2, 0.0)])
+    d = [oracle_mod.rollout(ai.Model(lead=0, a_cmd=a), p)["x_ref"][0]
+         for a in (-2.0, -4.0, -6.0, -8.0, -10.0)]
+    assert all(d[i] > d[i + 1] for i in range(len(d) - 1))
+
+
+# ---------------------------------------------------------------------------
+# Degenerate inputs
+# ---------------------------------------------------------------------------
+
+def test_edge_cases(oracle_mod):
+    m = ai.single_model()
+    p = ai.edge_params(m)
+    o = oracle_mod.rollout(m, p)
+    st = o["status"]
+    # already stopped / negative speed: stop at x = 0, t = 0
+    assert st[0] == 0 and o["x_ref"][0] == 0.0 and o["t_end"][0] == 0.0 and o["n_steps"][0] == 0
+    assert st[1] == 0 and o["x_ref"][1] == 0.0
+    # instantaneous actuator and no delay run to a normal stop
+    assert st[2] == 0 and st[3] == 0
+    assert o["x_ref"][2] > o["x_ref"][3]  # delay 0.2 s vs none, tau 0 vs 0.2: delay dominates
+    # no grip: drag alone cannot stop the car before the lead
+    assert st[4] == 1
+    # gap already zero / lead behind: contact at t = 0 with the initial speed
+    assert st[5] == 1 and o["t_end"][5] == 0.0 and o["v_imp"][5] == 20.0
+    assert st[6] == 1 and o["x_ref"][6] == 0.0
+    # downhill crawl on ice: the horizon ends the run
+    assert st[7] == 2 and o["t_end"][7] == 10.0 and o["n_steps"][7] == 10000
+    assert st[8] in (0, 1) and st[9] == 0 and o["x_ref"][9] < 1e-5
+    assert st[10] in (0, 1) and st[11] in (0, 1)
+    # invalid samples are flagged and carry NaN outputs
+    assert np.all(st[12:] == 255)
+    assert np.all(np.isnan(o["x_ref"][12:])) and np.all(o["n_steps"][12:] == 0)
+
+
+def test_steps_to_reach(oracle_mod):
+    assert oracle_mod.steps_to_reach(10.0, 1e-3) == 10000
+    assert oracle_mod.steps_to_reach(10.0, 1e-4) == 100000
+    assert oracle_mod.steps_to_reach(0.0, 1e-3) == 0
+    rng = np.random.default_rng(0)
+    for t in rng.uniform(0, 0.5, 500):
+        n = oracle_mod.steps_to_reach(t, 1e-3)
+        assert n * 1e-3 >= t and (n == 0 or (n - 1) * 1e-3 < t)

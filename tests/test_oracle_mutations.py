@@ -1,0 +1,52 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake in a copy of the oracle source (on the CPU, in a temporary directory),
+builds it, and runs the oracle pin tests against that build in a child
+process: at least one pin has to fail."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "aeb_oracle.c")
+
+MUTATIONS = [
+    ("grade sign", "return ((-r) - (c->k * v) * v) - c->gs;",
+     "return ((-r) - (c->k * v) * v) + c->gs;"),
+    ("dropped drag", "return ((-r) - (c->k * v) * v) - c->gs;", "return (-r) - c->gs;"),
+    ("RK4 stage 3 step", "double v3 = v + h2 * kv2;", "double v3 = v + dt * kv2;"),
+    ("RK4 position weights", "double xn = x + h6 * (((v + 2.0 * v2) + 2.0 * v3) + v4);",
+     "double xn = x + h6 * (((v + 2.0 * v2) + 2.0 * v2) + v4);"),
+    ("front brake share", "c->f1 = (1.0 - m->beta) / (1.0 - mh);",
+     "c->f1 = (m->beta) / (1.0 - mh);"),
+    ("Eq. 5 sign", "c->cap = (mu * m->g) / (1.0 + mh);", "c->cap = (mu * m->g) / (1.0 - mh);"),
+    ("no stop refinement", "double s = v / (v - vn);", "double s = 1.0;"),
+    ("actuator stage", "ka2 = (u - a2) * c->it;", "ka2 = (u - a1) * c->it;"),
+    ("TTC threshold", "if (gap_meas <= m->ttc_thr * v)", "if (gap_meas < m->ttc_thr * v - 0.01)"),
+    ("onset rounding", "c->n_delay = om_steps_to_reach(td, m->dt);",
+     "c->n_delay = (int64_t)(td / m->dt);"),
+    ("impact speed", "*v_imp = v + s * (vn - v);", "*v_imp = vn;"),
+    ("Box-Muller angle word", "double u2 = (double)(w1 >> 11) * two_m53;",
+     "double u2 = (double)(w0 >> 11) * two_m53;"),
+    ("contact test", "if (m->lead && xn >= c->d0) {", "if (m->lead && xn > c->d0 + 1e-3) {"),
+    ("Philox key schedule", "if (round > 0) { k0 += W0; k1 += W1; }", "if (round > 0) { k0 += W0; }"),
+    ("histogram origin", "double q = floor((x - lo) / w);", "double q = floor(x / w);"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old}"
+    mutated = tmp_path / "m.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "m.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                    str(so), str(mutated), "-lm"], check=True)
+    env = dict(os.environ, AEB_ORACLE_SO=str(so))
+    tests = [os.path.join(ROOT, "tests", f) for f in
+             ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py")]
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        *tests], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"mutation '{name}' survived:\n{r.stdout[-2000:]}"
