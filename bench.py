@@ -1,0 +1,311 @@
+"""Benchmark: Monte Carlo AEB braking rollouts per second on GB300.
+
+Workload: one scenario with the single-scenario distributions (v0~U(15,35),
+d0~N(60,5) in [30,90], mu~U(0.4,0.9), grade~N(0,0.02), m~N(1600,100),
+Cd~U(0.28,0.35), tau~U(0.1,0.3), delay~U(0.1,0.3), range noise~N(0,0.5);
+per-axle caps, lead at d0, dt = 1 ms, 10 s horizon), N = 1e7 samples: the
+largest point of the throughput sweep over N = 1e3..1e7.  Parameters are drawn
+by the library's seeded host sampler and are resident in HBM when timing starts.
+
+A step = one pass of the hot path: the FP32-compensated rollout of all N
+samples plus the deterministic reduction to counts, moments and histograms.
+`value` is rollouts/s of that step; the FP64-plain path is timed on the same
+samples and reported beside it ("fp64_plain").  `e2e` is the same metric
+through aeb_evaluate (pinned host parameters in, host stats out, copies in
+the timed region).  The inputs (800 MB of parameters) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+`--impl reference` times the plain CPU oracle on a bounded sample of the same
+workload on the host cores (the CPU baseline), with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import aeb_inputs as ai  # noqa: E402
+
+METRIC = "rollouts/sec FP32-comp vs FP64 plain on 1 GB300; p99 request latency vs 530 ms"
+UNIT = "rollouts/s"
+# Algorithmic binary64 operations (add, subtract, multiply) of one RK4 step of
+# the per-axle model in the plain definition: actuator 21, four accelerations
+# 4 x 8, three stage speeds 6, position and speed updates 7 + 7.  min and
+# comparisons are not counted.
+FLOPS_PER_STEP = 73
+SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.t.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4)
+                          if r[3 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(model, scenario, n_sample: int):
+    """The oracle as it stands, on all host cores, on the first n_sample samples
+    of the workload (the same sampler stream); extrapolated per rollout."""
+    import oracle
+    cores = os.cpu_count() or 1
+    p = oracle.sample(model, scenario, 0, n_sample)
+    t0 = time.perf_counter()
+    out = oracle.rollout(model, p, threads=cores)
+    dt = time.perf_counter() - t0
+    steps = int(out["n_steps"].astype(np.int64).sum())
+    return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample} of the N-sample workload (same seed), "
+                      f"{steps} RK4 steps, {dt:.2f} s wall on {cores} threads",
+            "steps_per_s": steps / dt}
+
+
+def config(args, world):
+    return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
+                        "10 s horizon, lead at d0, per-axle caps, immediate trigger",
+            "n_samples_per_gpu": args.n, "dt_s": args.dt, "precision": "fp32-compensated",
+            "l2": "inputs 800 MB per GPU > 129 MB L2, no flush",
+            "parallelism": f"replicas x{world} (independent sample shards)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    m = ai.single_model(dt=args.dt)
+    sc = ai.single_scenario(seed=0)
+    import oracle
+    cores = os.cpu_count() or 1
+    n_step = max(1000, args.cpu_sample // 2)
+    p = oracle.sample(m, sc, 0, n_step)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.rollout(m, {f: v[:2000] for f, v in p.items()}, threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rollout(m, p, threads=cores)
+    dt = time.perf_counter() - t0
+    v = n_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, world),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n_step} samples of the workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2604_27193_gb300 as aeb
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    aeb.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    N = args.n
+    m = ai.single_model(dt=args.dt)
+    sc = ai.replace(ai.single_scenario(seed=0), scenario_id=rank)  # each rank its own shard
+
+    # host sampling into pinned buffers, then resident device copies
+    t0 = time.perf_counter()
+    host = aeb.alloc_params(N, device="cpu", pin=True)
+    aeb.aeb_sample_params(m, sc, 0, N, host)
+    t_sample = time.perf_counter() - t0
+    P = {f: host[f].to(dev, non_blocking=True) for f in ai.FIELDS}
+    O = aeb.alloc_outputs(N, device=dev, which=("status", "x_ref", "v_imp", "n_steps"))
+    S = aeb.alloc_stats(dev)
+    hist = aeb.hist_spec()
+    torch.cuda.synchronize()
+
+    def step(prec):
+        aeb.aeb_rollout(m, P, N, prec, O, stream)
+        aeb.aeb_reduce(O, N, hist, S, stream)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: FP32-compensated step -------------------------------
+    for _ in range(args.warmup):
+        step(aeb.FP32_COMP)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for e0, e1, e2 in ev:
+            e0.record(stream)
+            aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O, stream)
+            e1.record(stream)
+            aeb.aeb_reduce(O, N, hist, S, stream)
+            e2.record(stream)
+        end.record(stream)
+        barrier()
+    ms_total = max_over_ranks(start.elapsed_time(end))
+    roll_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1, _ in ev)
+    red_ms = statistics.mean(e1.elapsed_time(e2) for _, e1, e2 in ev)
+    st = aeb.stats_from_buffer(S)
+    steps_per_launch = int(st.steps)
+    value = world * N * args.steps / (ms_total / 1e3)
+    achieved = steps_per_launch * FLOPS_PER_STEP / (roll_ms / 1e3) / 1e12
+
+    # ---- FP64 plain on the same samples ----------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        for _ in range(1):
+            step(aeb.FP64_PLAIN)
+        barrier()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.fp64_steps):
+            step(aeb.FP64_PLAIN)
+        s1.record(stream)
+        barrier()
+        ms64 = max_over_ranks(s0.elapsed_time(s1)) / args.fp64_steps
+        fp64 = {"value": world * N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "steps": args.fp64_steps, "warmup": 1, "dtype": "f64",
+                "achieved_tflops": steps_per_launch * FLOPS_PER_STEP / (ms64 / 1e3) / 1e12,
+                "peak_tflops_nominal": FP64_PEAK_TFLOPS}
+
+    # ---- end to end through the public host-buffer call ------------------
+    aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)  # sizes the buffers
+    barrier()
+    e2e_steps = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * N * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * len(ai.FIELDS) * N, "d2h_bytes_per_step": aeb.STATS_BYTES,
+           "api": "aeb_evaluate (pinned host params -> host stats)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config(args, world),
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "kernel": "k_rollout_fp32", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts, max clock)",
+                     "flops_per_launch": steps_per_launch * FLOPS_PER_STEP,
+                     "launch_ms": roll_ms},
+        "kernels_ms": {"rollout_fp32": roll_ms, "reduce": red_ms},
+        "fp64_plain": fp64,
+        "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
+        "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
+        "steps_per_rollout": steps_per_launch / N,
+        "host_sampling_s": t_sample,
+        "stats": {"n_stop": int(st.n_stop), "n_contact": int(st.n_contact),
+                  "n_horizon": int(st.n_horizon), "p_contact": st.n_contact / st.n},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, sc, args.cpu_sample)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * aeb.h -- C ABI of the GB300 Monte Carlo AEB braking library (libaeb.so).
+ *
+ * The library evaluates independent Monte Carlo emergency-braking rollouts of a
+ * longitudinal vehicle model and reduces them to stopping, collision and
+ * impact-speed statistics, after Karjol & Alawneh, "Real-Time GPU-Accelerated
+ * Monte Carlo Evaluation of Safety-Critical AEB Systems Under Uncertainty":
+ *   model ................ Sec. III, Eq. 1-9 (drag, grade, weight transfer, lag)
+ *   sampling ............. Sec. IV-A..IV-C, Eq. 10-15 (seeded, on the host)
+ *   integration .......... Sec. IV-D (fixed-step RK4), Sec. V-D (v <= 0)
+ *   one rollout per lane . Sec. V-A..V-C
+ *   statistics ........... Sec. VI-B (mean, std, range), Sec. VI-C, Eq. 19
+ *                          (P(D_stop > H0), safe headways)
+ * The lead vehicle, reaction delay, range noise, per-axle friction caps and
+ * the TTC trigger extend the paper's model; each struct field says so.
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only; pointers are host or device as each argument says.
+ *   - Buffers passed in are owned by the caller and never freed or retained by
+ *     the library after the call's stream work completes.  Library-owned
+ *     scratch is allocated on first use per device and reused.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls marked
+ *     "asynchronous" only enqueue work on it; results are valid once the
+ *     stream has reached that point.
+ *   - Every call returns an aeb_status; on failure aeb_last_error() gives a
+ *     message (thread-local, valid until the next call on the same thread).
+ *     Invalid arguments never reach the GPU.
+ */
+#ifndef AEB_H
+#define AEB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AEB_ABI_VERSION 1
+#define AEB_NFIELDS 10   /* columns of a parameter set, see aeb_params       */
+#define AEB_NBINS 4096   /* bins of each fixed histogram in aeb_stats         */
+
+/* ---- status codes ------------------------------------------------------- */
+typedef int32_t aeb_status;
+enum {
+    AEB_OK = 0,
+    AEB_EINVAL = 1,      /* an argument is out of its documented domain       */
+    AEB_ENOMEM = 2,      /* host or device allocation failed                   */
+    AEB_ECUDA = 3,       /* a CUDA runtime call failed (message says which)   */
+    AEB_ETIMEOUT = 4,    /* a bounded wait ran out                             */
+    AEB_EAGAIN = 5,      /* result not ready yet                               */
+    AEB_ECANCELLED = 6,  /* the request was cancelled                          */
+    AEB_EDEVICE = 7      /* no usable CUDA device / wrong architecture         */
+};
+
+/* ---- enumerations ------------------------------------------------------- */
+typedef int32_t aeb_precision;
+enum {
+    AEB_FP64_PLAIN = 0,  /* binary64, no fused multiply-add: bit-identical to
+                            the plain CPU definition (Sec. V-D)               */
+    AEB_FP32_COMP = 1    /* binary32 stages with compensated (double-float)
+                            position and speed; FP64 stop/contact refinement  */
+};
+enum { AEB_CAP_LUMPED = 0, AEB_CAP_PER_AXLE = 1 };
+enum { AEB_TRIGGER_IMMEDIATE = 0, AEB_TRIGGER_TTC = 1 };
+enum { AEB_STOP = 0, AEB_CONTACT = 1, AEB_HORIZON = 2, AEB_INVALID = 255 };
+enum { AEB_DIST_CONST = 0, AEB_DIST_UNIFORM = 1, AEB_DIST_NORMAL = 2 };
+
+/* ---- model constants (Sec. III, Sec. IV-B) ------------------------------- */
+typedef struct aeb_model {
+    double g;          /* gravitational acceleration [m/s^2]                      */
+    double rho;        /* air density [kg/m^3] (Eq. 4)                            */
+    double area;       /* frontal area A_f [m^2] (Eq. 4)                          */
+    double h_cg;       /* centre-of-gravity height h [m] (Eq. 5)                  */
+    double wheelbase;  /* wheelbase L [m] (Eq. 5)                                 */
+    double beta;       /* front share of the demanded brake force (per-axle caps) */
+    double phi_f;      /* static front share of the normal load (per-axle caps)   */
+    double a_cmd;      /* commanded braking acceleration, negative [m/s^2] (Eq. 2) */
+    double dt;         /* RK4 step [s] (Sec. IV-B), > 0                            */
+    double t_max;      /* horizon [s] (Sec. IV-B), >= 0                            */
+    double ttc_thr;    /* TTC trigger threshold [s] (TTC = H0 / v, Sec. VI-C)     */
+    int32_t cap_mode;  /* AEB_CAP_LUMPED: Eq. 5 as printed, r <= mu g/(1+mu h/L);
+                          AEB_CAP_PER_AXLE: front/rear forces capped at mu N per
+                          axle with weight transfer (extension)                  */
+    int32_t trigger;   /* AEB_TRIGGER_IMMEDIATE: brake after the reaction delay;
+                          AEB_TRIGGER_TTC: brake once the measured gap
+                          (d0 - x + noise) <= ttc_thr * v, then the delay        */
+    int32_t lead;      /* 1: stationary lead vehicle at d0 (contact ends a run)  */
+    int32_t reserved;  /* must be 0                                             */
+} aeb_model;
+
+/* ---- sampling description (Sec. IV-A, IV-C) ------------------------------ */
+typedef struct aeb_dist {
+    int32_t kind;      /* AEB_DIST_*                                             */
+    int32_t reserved;  /* must be 0                                             */
+    double p0, p1;     /* const: p0 | uniform: [p0, p1) | normal: mean p0, sd p1  */
+    double lo, hi;     /* every draw is clamped to [lo, hi] (+-inf: no clamp)    */
+} aeb_dist;
+
+typedef struct aeb_scenario {
+    aeb_dist v0;       /* initial speed [m/s]                 (Eq. 11)          */
+    aeb_dist d0;       /* initial gap to the lead [m]         (extension)       */
+    aeb_dist mu;       /* tyre-road friction coefficient      (Eq. 12)          */
+    aeb_dist grade;    /* road grade angle [rad]              (Eq. 13)          */
+    aeb_dist mass;     /* vehicle mass [kg]                   (Eq. 14)          */
+    aeb_dist cd;       /* drag coefficient                    (Eq. 15)          */
+    aeb_dist tau;      /* actuator time constant [s]          (Eq. 6)           */
+    aeb_dist t_delay;  /* reaction delay before braking [s]   (extension)       */
+    aeb_dist noise;    /* constant range-measurement bias [m] (extension)       */
+    uint64_t seed;     /* Philox-4x64-10 key word 0                             */
+    uint64_t scenario_id; /* Philox-4x64-10 key word 1                          */
+} aeb_scenario;
+
+/* Structure-of-arrays parameter sets xi^(i) (Eq. 10): ten float64 columns of
+ * the same length, sample i at index i of each.  gs = g sin(theta) and
+ * gc = g cos(theta) are taken on the host so the device never evaluates a
+ * transcendental.  Columns are host or device memory as each call states;
+ * each column must be 8-byte aligned. */
+typedef struct aeb_params {
+    double *v0, *d0, *mu, *gs, *gc, *mass, *cd, *tau, *t_delay, *noise;
+} aeb_params;
+
+/* Per-sample outputs, one entry per sample.  Any pointer may be NULL (that
+ * output is not stored); aeb_reduce needs status, x_ref, v_imp, n_steps.
+ *   status  AEB_STOP / AEB_CONTACT / AEB_HORIZON / AEB_INVALID
+ *   x_raw   x at the end of the terminating step: the paper's D_stop (Eq. 3)
+ *   x_ref   position at the refined stop or contact instant (contact: d0)
+ *   v_imp   speed at contact (0 unless AEB_CONTACT)
+ *   t_end   refined time of the stop / contact / horizon [s]
+ *   n_steps RK4 steps executed
+ *   n_onset first step with the braking command applied (-1: never issued)
+ * Invalid samples (non-finite field, mass <= 0, tau/mu/cd/t_delay < 0) get
+ * AEB_INVALID, NaN values and n_steps = 0. */
+typedef struct aeb_outputs {
+    uint8_t *status;
+    double *x_raw, *x_ref, *v_imp, *t_end;
+    int32_t *n_steps, *n_onset;
+} aeb_outputs;
+
+/* Fixed-bin histograms: bin j of D holds floor((x_ref - lo_d) / w_d) == j over
+ * stopped samples, bin j of V the same for v_imp over contact samples, the
+ * index clamped to [0, AEB_NBINS - 1].  Widths must be powers of two. */
+typedef struct aeb_hist_spec {
+    double lo_d, w_d, lo_v, w_v;
+} aeb_hist_spec;
+
+/* Reduction of a set of outputs (Sec. VI-B, VI-C). */
+typedef struct aeb_stats {
+    uint64_t n, n_stop, n_contact, n_horizon, n_invalid;
+    uint64_t steps;                       /* sum of n_steps                    */
+    double sum_d, sumsq_d, min_d, max_d;  /* x_ref over stopped samples        */
+    double sum_v, sumsq_v, min_v, max_v;  /* v_imp over contact samples        */
+    double lo_d, w_d, lo_v, w_v;          /* the histogram spec used           */
+    uint64_t hist_d[AEB_NBINS];
+    uint64_t hist_v[AEB_NBINS];
+} aeb_stats;
+
+/* ---- entry points -------------------------------------------------------- */
+
+/* ABI version of the loaded library (AEB_ABI_VERSION when it was built). */
+int32_t aeb_abi_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *aeb_last_error(void);
+
+/*
+ * aeb_sample_params -- draw parameter sets xi^(first) .. xi^(first+n-1)
+ * (Sec. IV-A, IV-C: random numbers drawn on the host from a fixed seed).
+ * Sample i, quantity q uses Philox-4x64-10 block (counter (i, q/2, 0, 0),
+ * key (seed, scenario_id)), words 0-1 for even q and 2-3 for odd q, in the
+ * quantity order of aeb_scenario.  Uniform: p0 + (p1 - p0) U, U = (w0>>11)
+ * 2^-53.  Normal: p0 + p1 sqrt(-2 ln U1) cos(2 pi U2), U1 = ((w0>>11)+1) 2^-53,
+ * U2 = (w1>>11) 2^-53.  Then clamp.  gs, gc = g sin(grade), g cos(grade).
+ *   model    host; only model->g is read
+ *   out      host columns (caller-owned, >= n doubles each)
+ *   n_threads host threads to use (<= 0: all hardware threads)
+ * Synchronous, host only.  Output is independent of n_threads.
+ * AEB_EINVAL: NULL pointer, unknown distribution kind, non-finite parameter.
+ */
+aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenario *scenario,
+                             uint64_t first, uint64_t n, const aeb_params *out,
+                             int32_t n_threads);
+
+/*
+ * aeb_rollout -- integrate every sample until contact, stop or horizon
+ * (Sec. IV-D RK4 of Eq. 7-9, termination Sec. V-D) and write per-sample
+ * outputs.  One CUDA lane owns one rollout at a time (Sec. V-A); lanes whose
+ * rollout ends pick up the next sample of their warp's tile.
+ *   model      host
+ *   params     device columns, n entries each (caller-owned)
+ *   precision  AEB_FP64_PLAIN: every output bit-identical to the plain binary64
+ *              definition; AEB_FP32_COMP: see the precision enum
+ *   out        device columns (caller-owned; NULL members are skipped)
+ *   stream     cudaStream_t
+ * Asynchronous.  n == 0 is a no-op.
+ * AEB_EINVAL: NULL params column, bad model (non-finite constant, dt <= 0,
+ * t_max < 0, t_max/dt beyond 2^31 - 2 steps, unknown mode, reserved != 0,
+ * wheelbase <= 0), unknown precision, misaligned column.
+ * AEB_ECUDA / AEB_EDEVICE on launch failure.
+ */
+aeb_status aeb_rollout(const aeb_model *model, const aeb_params *params, uint64_t n,
+                       aeb_precision precision, const aeb_outputs *out, void *stream);
+
+/*
+ * aeb_reduce -- counts, moments, extremes and fixed-bin histograms of a set of
+ * outputs (Sec. VI-B; Sec. VI-C reads P(D_stop > H0) off hist_d at bin edges).
+ * Sums are taken in a fixed order that depends only on n, so repeated calls
+ * give identical bits.
+ *   out        device columns status, x_ref, v_imp, n_steps (n entries)
+ *   hist       host
+ *   stats      DEVICE pointer to one aeb_stats (caller-owned, 8-byte aligned)
+ * Asynchronous.  Uses library scratch on the stream's device.
+ * AEB_EINVAL: NULL column, width not a positive power of two, non-finite lo.
+ */
+aeb_status aeb_reduce(const aeb_outputs *out, uint64_t n, const aeb_hist_spec *hist,
+                      aeb_stats *stats, void *stream);
+
+/*
+ * aeb_evaluate -- the whole path from host buffers: copy the parameter columns
+ * to device buffers owned by the library, roll out, reduce, copy the stats
+ * (and the requested per-sample outputs) back, and wait for the stream.
+ *   params      HOST columns (pinned memory gives the fastest copies)
+ *   host_stats  host aeb_stats written on success
+ *   host_out    host columns for per-sample outputs, or NULL / NULL members
+ * Synchronous.  AEB_ENOMEM if the device buffers cannot be grown.
+ */
+aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64_t n,
+                        aeb_precision precision, const aeb_hist_spec *hist,
+                        aeb_stats *host_stats, const aeb_outputs *host_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AEB_H */

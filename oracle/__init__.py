@@ -87,7 +87,8 @@ def lib():
                                     P(P(C.c_double))]
             L.om_rollout.argtypes = [P(_Model), P(P(C.c_double)), C.c_uint64,
                                      P(C.c_uint8), P(C.c_double), P(C.c_double),
-                                     P(C.c_double), P(C.c_double), P(C.c_int32)]
+                                     P(C.c_double), P(C.c_double), P(C.c_int32),
+                                     P(C.c_int32)]
             L.om_reduce.argtypes = [C.c_uint64, P(C.c_uint8), P(C.c_double), P(C.c_double),
                                     P(C.c_int32), P(_Stats),
                                     P(C.c_uint64), C.c_double, C.c_double,
@@ -169,6 +170,7 @@ def rollout(model, params: dict, threads: int = 1) -> dict:
         "v_imp": np.empty(n, dtype=np.float64),
         "t_end": np.empty(n, dtype=np.float64),
         "n_steps": np.empty(n, dtype=np.int32),
+        "n_onset": np.empty(n, dtype=np.int32),
     }
     m = _model(model)
     L = lib()
@@ -180,7 +182,8 @@ def rollout(model, params: dict, threads: int = 1) -> dict:
                      C.cast(C.c_void_p(out["status"].ctypes.data + lo), P(C.c_uint8)),
                      *[C.cast(C.c_void_p(out[k].ctypes.data + 8 * lo), P(C.c_double))
                        for k in ("x_raw", "x_ref", "v_imp", "t_end")],
-                     C.cast(C.c_void_p(out["n_steps"].ctypes.data + 4 * lo), P(C.c_int32)))
+                     C.cast(C.c_void_p(out["n_steps"].ctypes.data + 4 * lo), P(C.c_int32)),
+                     C.cast(C.c_void_p(out["n_onset"].ctypes.data + 4 * lo), P(C.c_int32)))
         del keep
 
     threads = max(1, min(int(threads), n)) if n else 1

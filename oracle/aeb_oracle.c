@@ -198,7 +198,9 @@ static double dmin(double a, double b) { return (b < a) ? b : a; }
 int64_t om_steps_to_reach(double t, double dt)
 {
     if (!(t > 0.0)) return 0;
-    int64_t n = (int64_t)ceil(t / dt);
+    double q = ceil(t / dt);
+    if (!(q <= 2147483647.0)) return 2147483647;  /* beyond any representable horizon */
+    int64_t n = (int64_t)q;
     while (n > 0 && (double)(n - 1) * dt >= t) --n;
     while ((double)n * dt < t) ++n;
     return n;
@@ -312,14 +314,17 @@ double om_axle_cap(const om_model *m, double mu, double gc, double D)
  *
  * Termination after step n -> n+1, in this order: contact if a lead is
  * present and x_{n+1} >= d0; stop if v_{n+1} <= 0; horizon if n+1 == N_max.
- * Outputs: x_raw = x_{n+1} (the paper's D_stop = x(t_stop), Eq. 3);
+ * Outputs: n_onset = n_b once the command is issued (immediate trigger: always
+ *   n_delay; TTC trigger: -1 if it never fires), x_raw = x_{n+1} (the paper's
+ *   D_stop = x(t_stop), Eq. 3);
  *   stop:    s = v_n / (v_n - v_{n+1}),  x_ref = x_n + s (x_{n+1} - x_n)
  *   contact: s = (d0 - x_n) / (x_{n+1} - x_n), x_ref = d0,
  *            v_imp = v_n + s (v_{n+1} - v_n)
  *   t_end = (n + s) dt;  horizon: s = 1, x_ref = x_{n+1}.
  */
 static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, double *x_raw,
-                        double *x_ref, double *v_imp, double *t_end, int32_t *n_steps)
+                        double *x_ref, double *v_imp, double *t_end, int32_t *n_steps,
+                        int32_t *n_onset)
 {
     const double dt = m->dt;
     const double h2 = 0.5 * dt;
@@ -328,6 +333,7 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
 
     double x = 0.0, v = c->v0, a = 0.0;
     *v_imp = 0.0;
+    *n_onset = (m->trigger == OM_TRIGGER_IMMEDIATE) ? (int32_t)c->n_delay : -1;
     if (m->lead && c->d0 <= 0.0) {
         *status = OM_CONTACT; *x_raw = 0.0; *x_ref = 0.0; *v_imp = v;
         *t_end = 0.0; *n_steps = 0; return;
@@ -344,7 +350,10 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
     for (int64_t n = 0;; ++n) {
         if (!triggered) {
             double gap_meas = (c->d0 - x) + c->noise;
-            if (gap_meas <= m->ttc_thr * v) { triggered = 1; n_b = n + c->n_delay; }
+            if (gap_meas <= m->ttc_thr * v) {
+                triggered = 1; n_b = n + c->n_delay;
+                *n_onset = (n_b > 2147483647) ? 2147483647 : (int32_t)n_b;
+            }
         }
         double u = (triggered && n >= n_b) ? m->a_cmd : 0.0;
 
@@ -394,16 +403,17 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
 
 int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t n,
                uint8_t *status, double *x_raw, double *x_ref, double *v_imp, double *t_end,
-               int32_t *n_steps)
+               int32_t *n_steps, int32_t *n_onset)
 {
     for (uint64_t i = 0; i < n; ++i) {
         om_consts c;
         if (!make_consts(m, cols, i, &c)) {
             status[i] = OM_INVALID; x_raw[i] = NAN; x_ref[i] = NAN; v_imp[i] = NAN;
-            t_end[i] = NAN; n_steps[i] = 0;
+            t_end[i] = NAN; n_steps[i] = 0; n_onset[i] = -1;
             continue;
         }
-        rollout_one(m, &c, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i], &n_steps[i]);
+        rollout_one(m, &c, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i], &n_steps[i],
+                    &n_onset[i]);
     }
     return 0;
 }

@@ -1,0 +1,296 @@
+"""Python binding of libaeb (GB300 Monte Carlo AEB braking rollouts).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels and host sampler.  The entry points have the names of the C ABI
+declared in ``include/aeb.h``.  PyTorch is used for device memory and streams.
+
+Importing this package does not build anything; call ``build()`` first (or
+``python -m paper_2604_27193_gb300._build``).  If the library is missing the
+import of ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+FIELDS = ("v0", "d0", "mu", "gs", "gc", "mass", "cd", "tau", "t_delay", "noise")
+QUANTITIES = ("v0", "d0", "mu", "grade", "mass", "cd", "tau", "t_delay", "noise")
+OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
+OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
+              "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
+              "n_onset": np.int32}
+NBINS = 4096
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)
+FP64_PLAIN, FP32_COMP = 0, 1
+STOP, CONTACT, HORIZON, INVALID = 0, 1, 2, 255
+
+
+class AebError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"aeb status {code}: {msg}")
+        self.code = code
+
+
+# --------------------------------------------------------------------------
+# ctypes mirrors of include/aeb.h
+# --------------------------------------------------------------------------
+
+class Model(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "g", "rho", "area", "h_cg", "wheelbase", "beta", "phi_f", "a_cmd", "dt", "t_max",
+        "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "reserved")]
+
+
+class Dist(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("p0", C.c_double),
+                ("p1", C.c_double), ("lo", C.c_double), ("hi", C.c_double)]
+
+
+class Scenario(C.Structure):
+    _fields_ = [(q, Dist) for q in QUANTITIES] + [("seed", C.c_uint64),
+                                                   ("scenario_id", C.c_uint64)]
+
+
+class Params(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in FIELDS]
+
+
+class Outputs(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in OUTPUTS]
+
+
+class HistSpec(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("lo_d", "w_d", "lo_v", "w_v")]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n", "n_stop", "n_contact", "n_horizon",
+                                          "n_invalid", "steps")] + \
+        [(n, C.c_double) for n in ("sum_d", "sumsq_d", "min_d", "max_d", "sum_v", "sumsq_v",
+                                   "min_v", "max_v", "lo_d", "w_d", "lo_v", "w_v")] + \
+        [("hist_d", C.c_uint64 * NBINS), ("hist_v", C.c_uint64 * NBINS)]
+
+
+STATS_BYTES = C.sizeof(Stats)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded libaeb.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"libaeb.so is not built ({_build.LIB}); run "
+                                  "paper_2604_27193_gb300.build() first")
+            L = C.CDLL(_build.LIB)
+            P = C.POINTER
+            L.aeb_abi_version.restype = C.c_int32
+            L.aeb_last_error.restype = C.c_char_p
+            L.aeb_sample_params.argtypes = [P(Model), P(Scenario), C.c_uint64, C.c_uint64,
+                                            P(Params), C.c_int32]
+            L.aeb_rollout.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32, P(Outputs),
+                                      C.c_void_p]
+            L.aeb_reduce.argtypes = [P(Outputs), C.c_uint64, P(HistSpec), C.c_void_p,
+                                     C.c_void_p]
+            L.aeb_evaluate.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32,
+                                       P(HistSpec), P(Stats), P(Outputs), C.c_void_p]
+            for fn in ("aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate"):
+                getattr(L, fn).restype = C.c_int32
+            if L.aeb_abi_version() != 1:
+                raise ImportError("libaeb.so ABI version mismatch")
+            _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise AebError(code, lib().aeb_last_error().decode())
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+
+def model(m) -> Model:
+    """aeb_model from any object (or dict) with the model's attribute names."""
+    get = m.__getitem__ if isinstance(m, dict) else lambda k: getattr(m, k)
+    s = Model()
+    for name, _ in Model._fields_:
+        if name != "reserved":
+            setattr(s, name, get(name))
+    return s
+
+
+def scenario(sc) -> Scenario:
+    s = Scenario()
+    for q in QUANTITIES:
+        d = getattr(sc, q)
+        dst = getattr(s, q)
+        dst.kind, dst.p0, dst.p1, dst.lo, dst.hi = d.kind, d.p0, d.p1, d.lo, d.hi
+    s.seed, s.scenario_id = sc.seed, sc.scenario_id
+    return s
+
+
+def hist_spec(lo_d=0.0, w_d=0.125, lo_v=0.0, w_v=1.0 / 64.0) -> HistSpec:
+    return HistSpec(lo_d, w_d, lo_v, w_v)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def params_struct(cols: dict, offset: int = 0) -> Params:
+    p = Params()
+    for f in FIELDS:
+        col = cols[f]
+        item = col.element_size() if hasattr(col, "element_size") else col.itemsize
+        setattr(p, f, _ptr(col) + offset * item)
+    return p
+
+
+def outputs_struct(out: dict | None) -> Outputs:
+    o = Outputs()
+    for f in OUTPUTS:
+        setattr(o, f, _ptr(out.get(f)) if out else 0)
+    return o
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# --------------------------------------------------------------------------
+# entry points (names of the C ABI)
+# --------------------------------------------------------------------------
+
+def aeb_sample_params(m, sc, first: int, n: int, out: dict | None = None,
+                      n_threads: int = 0) -> dict:
+    """Host sampling into ``out`` (dict of float64 host arrays / pinned
+    tensors); allocates numpy columns when ``out`` is None."""
+    if out is None:
+        out = {f: np.empty(n, dtype=np.float64) for f in FIELDS}
+    ms, ss, ps = model(m), scenario(sc), params_struct(out)
+    _check(lib().aeb_sample_params(C.byref(ms), C.byref(ss), first, n, C.byref(ps), n_threads))
+    return out
+
+
+def aeb_rollout(m, params: dict, n: int, precision: int, out: dict, stream=None):
+    """Asynchronous rollout of ``n`` device-resident samples into ``out``."""
+    ms, ps, os_ = model(m), params_struct(params), outputs_struct(out)
+    _check(lib().aeb_rollout(C.byref(ms), C.byref(ps), n, precision, C.byref(os_),
+                             _stream(stream)))
+
+
+def aeb_reduce(out: dict, n: int, hist: HistSpec, stats_dev, stream=None):
+    """Asynchronous reduction into ``stats_dev`` (a device buffer of
+    ``STATS_BYTES`` bytes, e.g. a uint8 CUDA tensor)."""
+    os_ = outputs_struct(out)
+    _check(lib().aeb_reduce(C.byref(os_), n, C.byref(hist), _ptr(stats_dev), _stream(stream)))
+
+
+def aeb_evaluate(m, params_host: dict, n: int, precision: int, hist: HistSpec,
+                 host_out: dict | None = None, stream=None) -> Stats:
+    """Whole path from host columns; returns the stats (synchronous)."""
+    ms, ps = model(m), params_struct(params_host)
+    st = Stats()
+    os_ = outputs_struct(host_out) if host_out else None
+    _check(lib().aeb_evaluate(C.byref(ms), C.byref(ps), n, precision, C.byref(hist),
+                              C.byref(st), C.byref(os_) if os_ is not None else None,
+                              _stream(stream)))
+    return st
+
+
+# --------------------------------------------------------------------------
+# torch conveniences
+# --------------------------------------------------------------------------
+
+def alloc_params(n: int, device="cuda", pin: bool = False) -> dict:
+    import torch
+    if device == "cpu":
+        return {f: torch.empty(n, dtype=torch.float64, pin_memory=pin) for f in FIELDS}
+    return {f: torch.empty(n, dtype=torch.float64, device=device) for f in FIELDS}
+
+
+def alloc_outputs(n: int, device="cuda", which=OUTPUTS, pin: bool = False) -> dict:
+    import torch
+    tdt = {"status": torch.uint8, "x_raw": torch.float64, "x_ref": torch.float64,
+           "v_imp": torch.float64, "t_end": torch.float64, "n_steps": torch.int32,
+           "n_onset": torch.int32}
+    if device == "cpu":
+        return {f: torch.empty(n, dtype=tdt[f], pin_memory=pin) for f in which}
+    return {f: torch.empty(n, dtype=tdt[f], device=device) for f in which}
+
+
+def alloc_stats(device="cuda"):
+    import torch
+    return torch.empty(STATS_BYTES, dtype=torch.uint8, device=device)
+
+
+def stats_from_buffer(buf) -> Stats:
+    """Copy a device/host stats buffer into a Stats struct (synchronises)."""
+    raw = buf.cpu().numpy().tobytes() if hasattr(buf, "cpu") else bytes(buf)
+    return Stats.from_buffer_copy(raw)
+
+
+@dataclass
+class Summary:
+    n: int
+    n_stop: int
+    n_contact: int
+    n_horizon: int
+    n_invalid: int
+    steps: int
+    mean_d: float
+    std_d: float
+    min_d: float
+    max_d: float
+    mean_v: float
+    p_contact: float
+
+
+def summarize(st: Stats) -> Summary:
+    def mean_std(s, ss, k):
+        if k == 0:
+            return float("nan"), float("nan")
+        m = s / k
+        var = (ss - k * m * m) / (k - 1) if k > 1 else 0.0
+        return m, float(np.sqrt(max(var, 0.0)))
+    md, sd = mean_std(st.sum_d, st.sumsq_d, st.n_stop)
+    mv, _ = mean_std(st.sum_v, st.sumsq_v, st.n_contact)
+    return Summary(st.n, st.n_stop, st.n_contact, st.n_horizon, st.n_invalid, st.steps, md,
+                   sd, st.min_d, st.max_d, mv, st.n_contact / st.n if st.n else float("nan"))
+
+
+def hist_quantile(st: Stats, q: float) -> float:
+    """Upper edge of the stopping-distance bin that holds the q-quantile
+    (inverted-CDF definition), i.e. within one bin width above the exact
+    order statistic."""
+    h = np.frombuffer(bytes(st.hist_d), dtype=np.uint64).astype(np.int64)
+    k = int(np.ceil(q * st.n_stop))
+    k = min(max(k, 1), int(st.n_stop))
+    j = int(np.searchsorted(np.cumsum(h), k))
+    return st.lo_d + (j + 1) * st.w_d

@@ -1,0 +1,353 @@
+// capi.cpp -- the C ABI entry points other than sampling: argument checks,
+// conversion of the model to the kernels' form, library scratch, dispatch.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "aeb_internal.h"
+#include "host_util.h"
+
+namespace aeb {
+
+namespace {
+thread_local std::string t_error;
+}
+
+void clear_error() { t_error.clear(); }
+
+aeb_status fail(aeb_status code, const std::string &msg)
+{
+    t_error = msg;
+    return code;
+}
+
+namespace {
+
+aeb_status cuda_fail(cudaError_t e, const char *what)
+{
+    const aeb_status code = (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+                             e == cudaErrorNoKernelImageForDevice ||
+                             e == cudaErrorInvalidDevice)
+                                ? AEB_EDEVICE
+                                : (e == cudaErrorMemoryAllocation ? AEB_ENOMEM : AEB_ECUDA);
+    return fail(code, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                          cudaGetErrorString(e) + ")");
+}
+
+bool is_pow2(double w)
+{
+    if (!(w > 0.0) || !std::isfinite(w)) return false;
+    int ex = 0;
+    return std::frexp(w, &ex) == 0.5;
+}
+
+aeb_status check_model(const aeb_model *m, ModelDev *out)
+{
+    if (!m) return fail(AEB_EINVAL, "model is NULL");
+    const double v[] = {m->g, m->rho, m->area, m->h_cg, m->wheelbase, m->beta,
+                        m->phi_f, m->a_cmd, m->dt, m->t_max, m->ttc_thr};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(AEB_EINVAL, "model constant is not finite");
+    if (!(m->dt > 0.0)) return fail(AEB_EINVAL, "model.dt must be > 0");
+    if (m->t_max < 0.0) return fail(AEB_EINVAL, "model.t_max must be >= 0");
+    if (!(m->wheelbase > 0.0)) return fail(AEB_EINVAL, "model.wheelbase must be > 0");
+    if (m->cap_mode != AEB_CAP_LUMPED && m->cap_mode != AEB_CAP_PER_AXLE)
+        return fail(AEB_EINVAL, "model.cap_mode unknown");
+    if (m->trigger != AEB_TRIGGER_IMMEDIATE && m->trigger != AEB_TRIGGER_TTC)
+        return fail(AEB_EINVAL, "model.trigger unknown");
+    if (m->lead != 0 && m->lead != 1) return fail(AEB_EINVAL, "model.lead must be 0 or 1");
+    if (m->reserved != 0) return fail(AEB_EINVAL, "model.reserved must be 0");
+    const int64_t n_max = steps_to_reach_host(m->t_max, m->dt);
+    if (n_max > 2147483646) return fail(AEB_EINVAL, "model.t_max / model.dt exceeds 2^31 - 2 steps");
+    out->g = m->g;
+    out->rho = m->rho;
+    out->area = m->area;
+    out->hl = m->h_cg / m->wheelbase;
+    out->beta = m->beta;
+    out->phi_f = m->phi_f;
+    out->a_cmd = m->a_cmd;
+    out->dt = m->dt;
+    out->h2 = 0.5 * m->dt;
+    out->h6 = m->dt / 6.0;
+    out->ttc_thr = m->ttc_thr;
+    out->n_max = (int32_t)n_max;
+    out->cap_mode = m->cap_mode;
+    out->trigger = m->trigger;
+    out->lead = m->lead;
+    return AEB_OK;
+}
+
+aeb_status check_params(const aeb_params *p, ParamsDev *out)
+{
+    if (!p) return fail(AEB_EINVAL, "params is NULL");
+    const double *c[AEB_NFIELDS] = {p->v0, p->d0, p->mu, p->gs, p->gc,
+                                    p->mass, p->cd, p->tau, p->t_delay, p->noise};
+    for (int j = 0; j < AEB_NFIELDS; ++j) {
+        if (!c[j]) return fail(AEB_EINVAL, "params column is NULL");
+        if (reinterpret_cast<uintptr_t>(c[j]) % 8 != 0)
+            return fail(AEB_EINVAL, "params column is not 8-byte aligned");
+        out->col[j] = c[j];
+    }
+    return AEB_OK;
+}
+
+aeb_status check_hist(const aeb_hist_spec *h)
+{
+    if (!h) return fail(AEB_EINVAL, "hist spec is NULL");
+    if (!std::isfinite(h->lo_d) || !std::isfinite(h->lo_v))
+        return fail(AEB_EINVAL, "hist origin is not finite");
+    if (!is_pow2(h->w_d) || !is_pow2(h->w_v))
+        return fail(AEB_EINVAL, "hist width must be a positive power of two");
+    return AEB_OK;
+}
+
+OutDev out_dev(const aeb_outputs *o)
+{
+    OutDev d{};
+    if (o) {
+        d.status = o->status;
+        d.x_raw = o->x_raw;
+        d.x_ref = o->x_ref;
+        d.v_imp = o->v_imp;
+        d.t_end = o->t_end;
+        d.n_steps = o->n_steps;
+        d.n_onset = o->n_onset;
+    }
+    return d;
+}
+
+// Library scratch, one region per (device, stream): work on one stream is
+// ordered, so consecutive calls on a stream may reuse its region, while calls
+// on different streams never share one.
+struct Region {
+    void *base = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_mu;
+std::map<std::pair<int, uintptr_t>, Region> g_scratch;
+
+constexpr size_t kCounterBytes = 256;
+size_t partial_bytes() { return sizeof(RedPartial) * 1024; }
+
+aeb_status scratch_for(cudaStream_t s, size_t bytes, void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    Region &r = g_scratch[{dev, reinterpret_cast<uintptr_t>(s)}];
+    if (r.bytes < bytes) {
+        if (r.base) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(r.base);
+            r.base = nullptr;
+            r.bytes = 0;
+        }
+        e = cudaMalloc(&r.base, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(scratch)");
+        r.bytes = bytes;
+    }
+    *out = r.base;
+    return AEB_OK;
+}
+
+LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 256}};
+
+aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
+                        aeb_precision precision, const OutDev &od, cudaStream_t s)
+{
+    void *scratch = nullptr;
+    aeb_status st = scratch_for(s, kCounterBytes + partial_bytes(), &scratch);
+    if (st != AEB_OK) return st;
+    auto *counter = static_cast<unsigned long long *>(scratch);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+    const LaunchCfg &cfg = g_cfg[precision];
+    WorkDev w{n, (uint32_t)cfg.tile, counter};
+    e = (precision == AEB_FP64_PLAIN) ? launch_rollout_fp64(md, pd, od, w, cfg, s)
+                                      : launch_rollout_fp32(md, pd, od, w, cfg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
+    return AEB_OK;
+}
+
+aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &h,
+                       aeb_stats *stats, cudaStream_t s)
+{
+    void *scratch = nullptr;
+    aeb_status st = scratch_for(s, kCounterBytes + partial_bytes(), &scratch);
+    if (st != AEB_OK) return st;
+    auto *partials = reinterpret_cast<RedPartial *>(static_cast<char *>(scratch) + kCounterBytes);
+    cudaError_t e = launch_reduce(out->status, out->x_ref, out->v_imp, out->n_steps, n, h,
+                                  partials, stats, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reduce launch");
+    return AEB_OK;
+}
+
+// Device buffers of aeb_evaluate, one set per (device, stream).
+struct EvalBuffers {
+    void *base = nullptr;
+    uint64_t cap = 0;  // samples
+};
+std::map<std::pair<int, uintptr_t>, EvalBuffers> g_eval;
+
+constexpr size_t kEvalBytesPerSample = 8 * AEB_NFIELDS + 1 + 8 * 4 + 4 * 2;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+int64_t steps_to_reach_host(double t, double dt)
+{
+    if (!(t > 0.0)) return 0;
+    const double q = std::ceil(t / dt);
+    if (!(q <= 2147483647.0)) return 2147483647;
+    int64_t n = (int64_t)q;
+    while (n > 0 && (double)(n - 1) * dt >= t) --n;
+    while ((double)n * dt < t) ++n;
+    return n;
+}
+
+}  // namespace aeb
+
+using namespace aeb;
+
+extern "C" int32_t aeb_abi_version(void) { return AEB_ABI_VERSION; }
+
+extern "C" const char *aeb_last_error(void) { return t_error.c_str(); }
+
+extern "C" aeb_status aeb_rollout(const aeb_model *model, const aeb_params *params, uint64_t n,
+                                  aeb_precision precision, const aeb_outputs *out, void *stream)
+{
+    clear_error();
+    ModelDev md;
+    ParamsDev pd;
+    aeb_status st = check_model(model, &md);
+    if (st != AEB_OK) return st;
+    st = check_params(params, &pd);
+    if (st != AEB_OK) return st;
+    if (precision != AEB_FP64_PLAIN && precision != AEB_FP32_COMP)
+        return fail(AEB_EINVAL, "unknown precision");
+    if (n == 0) return AEB_OK;
+    return rollout_impl(md, pd, n, precision, out_dev(out), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" aeb_status aeb_reduce(const aeb_outputs *out, uint64_t n, const aeb_hist_spec *hist,
+                                 aeb_stats *stats, void *stream)
+{
+    clear_error();
+    if (!out || !stats) return fail(AEB_EINVAL, "aeb_reduce: NULL argument");
+    if (n > 0 && (!out->status || !out->x_ref || !out->v_imp || !out->n_steps))
+        return fail(AEB_EINVAL, "aeb_reduce: status, x_ref, v_imp and n_steps are required");
+    if (reinterpret_cast<uintptr_t>(stats) % 8 != 0)
+        return fail(AEB_EINVAL, "aeb_reduce: stats is not 8-byte aligned");
+    aeb_status st = check_hist(hist);
+    if (st != AEB_OK) return st;
+    return reduce_impl(out, n, *hist, stats, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64_t n,
+                                   aeb_precision precision, const aeb_hist_spec *hist,
+                                   aeb_stats *host_stats, const aeb_outputs *host_out,
+                                   void *stream)
+{
+    clear_error();
+    ModelDev md;
+    ParamsDev hp;
+    aeb_status st = check_model(model, &md);
+    if (st != AEB_OK) return st;
+    st = check_params(params, &hp);
+    if (st != AEB_OK) return st;
+    if (precision != AEB_FP64_PLAIN && precision != AEB_FP32_COMP)
+        return fail(AEB_EINVAL, "unknown precision");
+    st = check_hist(hist);
+    if (st != AEB_OK) return st;
+    if (!host_stats) return fail(AEB_EINVAL, "aeb_evaluate: host_stats is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    const uint64_t cap = n > 0 ? n : 1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        EvalBuffers &b = g_eval[{dev, reinterpret_cast<uintptr_t>(s)}];
+        if (b.cap < cap) {
+            if (b.base) {
+                e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+                cudaFree(b.base);
+                b.base = nullptr;
+                b.cap = 0;
+            }
+            const size_t bytes = align256(sizeof(aeb_stats)) + cap * kEvalBytesPerSample + 16 * 256;
+            e = cudaMalloc(&b.base, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(evaluate buffers)");
+            b.cap = cap;
+        }
+        base = b.base;
+    }
+    char *p = static_cast<char *>(base);
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += align256(bytes);
+        return r;
+    };
+    aeb_stats *dstats = reinterpret_cast<aeb_stats *>(take(sizeof(aeb_stats)));
+    aeb_params dp;
+    double **dcols[AEB_NFIELDS] = {&dp.v0, &dp.d0, &dp.mu, &dp.gs, &dp.gc,
+                                   &dp.mass, &dp.cd, &dp.tau, &dp.t_delay, &dp.noise};
+    for (int j = 0; j < AEB_NFIELDS; ++j) {
+        *dcols[j] = reinterpret_cast<double *>(take(8 * cap));
+        if (n > 0) {
+            e = cudaMemcpyAsync(*dcols[j], hp.col[j], 8 * n, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(params)");
+        }
+    }
+    aeb_outputs dout;
+    dout.status = reinterpret_cast<uint8_t *>(take(cap));
+    dout.x_raw = reinterpret_cast<double *>(take(8 * cap));
+    dout.x_ref = reinterpret_cast<double *>(take(8 * cap));
+    dout.v_imp = reinterpret_cast<double *>(take(8 * cap));
+    dout.t_end = reinterpret_cast<double *>(take(8 * cap));
+    dout.n_steps = reinterpret_cast<int32_t *>(take(4 * cap));
+    dout.n_onset = reinterpret_cast<int32_t *>(take(4 * cap));
+
+    ParamsDev pd;
+    check_params(&dp, &pd);
+    if (n > 0) {
+        aeb_outputs want = dout;
+        if (!host_out || !host_out->x_raw) want.x_raw = nullptr;
+        if (!host_out || !host_out->t_end) want.t_end = nullptr;
+        if (!host_out || !host_out->n_onset) want.n_onset = nullptr;
+        st = rollout_impl(md, pd, n, precision, out_dev(&want), s);
+        if (st != AEB_OK) return st;
+    }
+    st = reduce_impl(&dout, n, *hist, dstats, s);
+    if (st != AEB_OK) return st;
+    e = cudaMemcpyAsync(host_stats, dstats, sizeof(aeb_stats), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(stats)");
+    if (host_out && n > 0) {
+        struct {
+            void *h;
+            const void *d;
+            size_t sz;
+        } cp[] = {{host_out->status, dout.status, 1},   {host_out->x_raw, dout.x_raw, 8},
+                  {host_out->x_ref, dout.x_ref, 8},     {host_out->v_imp, dout.v_imp, 8},
+                  {host_out->t_end, dout.t_end, 8},     {host_out->n_steps, dout.n_steps, 4},
+                  {host_out->n_onset, dout.n_onset, 4}};
+        for (auto &c : cp) {
+            if (!c.h) continue;
+            e = cudaMemcpyAsync(c.h, c.d, c.sz * n, cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(outputs)");
+        }
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return AEB_OK;
+}

@@ -1,0 +1,216 @@
+// reduce.cu -- counts, moments, extremes and fixed-bin histograms of a set of
+// rollout outputs (Sec. VI-B statistics; Sec. VI-C reads P(D_stop > H0) and the
+// safe headways off the stopping-distance histogram).
+//
+// Two launches on the caller's stream:
+//   1. G blocks; block b owns samples [b*chunk, (b+1)*chunk).  Each thread
+//      walks its strided share in index order, the warp combines lanes with a
+//      fixed xor butterfly, warp 0 adds the warps in warp order, and the block
+//      writes one partial.  Histogram bins are counted with shared-memory
+//      atomics and flushed with 64-bit global atomics (integer adds commute,
+//      so they are exact and order-free).
+//   2. one block adds the G partials in the same fixed pattern.
+// G and chunk depend only on n, so the floating-point sums are the same bits
+// on every call.  The work is a single pass over 21 bytes per sample
+// (status, x_ref, v_imp, n_steps): bound by HBM bandwidth.
+#include <cfloat>
+
+#include "aeb_internal.h"
+
+namespace aeb {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedWarps = kRedThreads / 32;
+
+__device__ __forceinline__ int bin_index(double x, double lo, double inv_w)
+{
+    // floor((x - lo) / w) for a power-of-two width w: (x - lo) * (1 / w) is the
+    // same exact scaling, so the bin equals the division-based definition.
+    const double q = floor((x - lo) * inv_w);
+    if (!(q >= 0.0)) return 0;
+    if (q > (double)(AEB_NBINS - 1)) return AEB_NBINS - 1;
+    return (int)q;
+}
+
+__device__ __forceinline__ void init_partial(RedPartial &a)
+{
+    a.n_stop = a.n_contact = a.n_horizon = a.n_invalid = a.steps = 0;
+    a.sum_d = a.sumsq_d = a.sum_v = a.sumsq_v = 0.0;
+    a.min_d = a.min_v = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    a.max_d = a.max_v = __longlong_as_double(0xfff0000000000000ll);   // -inf
+}
+
+__device__ __forceinline__ void add_partial(RedPartial &a, const RedPartial &b)
+{
+    a.n_stop += b.n_stop;
+    a.n_contact += b.n_contact;
+    a.n_horizon += b.n_horizon;
+    a.n_invalid += b.n_invalid;
+    a.steps += b.steps;
+    a.sum_d += b.sum_d;
+    a.sumsq_d += b.sumsq_d;
+    a.sum_v += b.sum_v;
+    a.sumsq_v += b.sumsq_v;
+    a.min_d = fmin(a.min_d, b.min_d);
+    a.max_d = fmax(a.max_d, b.max_d);
+    a.min_v = fmin(a.min_v, b.min_v);
+    a.max_v = fmax(a.max_v, b.max_v);
+}
+
+__device__ __forceinline__ RedPartial shfl_xor_partial(const RedPartial &a, int m)
+{
+    RedPartial b;
+    b.n_stop = __shfl_xor_sync(0xffffffffu, a.n_stop, m);
+    b.n_contact = __shfl_xor_sync(0xffffffffu, a.n_contact, m);
+    b.n_horizon = __shfl_xor_sync(0xffffffffu, a.n_horizon, m);
+    b.n_invalid = __shfl_xor_sync(0xffffffffu, a.n_invalid, m);
+    b.steps = __shfl_xor_sync(0xffffffffu, a.steps, m);
+    b.sum_d = __shfl_xor_sync(0xffffffffu, a.sum_d, m);
+    b.sumsq_d = __shfl_xor_sync(0xffffffffu, a.sumsq_d, m);
+    b.sum_v = __shfl_xor_sync(0xffffffffu, a.sum_v, m);
+    b.sumsq_v = __shfl_xor_sync(0xffffffffu, a.sumsq_v, m);
+    b.min_d = __shfl_xor_sync(0xffffffffu, a.min_d, m);
+    b.max_d = __shfl_xor_sync(0xffffffffu, a.max_d, m);
+    b.min_v = __shfl_xor_sync(0xffffffffu, a.min_v, m);
+    b.max_v = __shfl_xor_sync(0xffffffffu, a.max_v, m);
+    return b;
+}
+
+// Combine a block's per-thread partials in a fixed pattern; result in thread 0.
+__device__ __forceinline__ RedPartial block_combine(RedPartial acc, RedPartial *sh)
+{
+    // butterfly: every lane ends with the same value, combined in a fixed order
+    for (int m = 16; m > 0; m >>= 1) {
+        RedPartial o = shfl_xor_partial(acc, m);
+        // order the two operands by lane so both lanes of a pair add a + b
+        const bool low = ((threadIdx.x & 31) & m) == 0;
+        RedPartial first = low ? acc : o, second = low ? o : acc;
+        add_partial(first, second);
+        acc = first;
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        RedPartial t = sh[0];
+        for (int j = 1; j < kRedWarps; ++j) add_partial(t, sh[j]);
+        acc = t;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
+                 const double *__restrict__ vi, const int32_t *__restrict__ ns, uint64_t n,
+                 uint64_t chunk, double lo_d, double inv_wd, double lo_v, double inv_wv,
+                 RedPartial *__restrict__ part, unsigned long long *__restrict__ hist_d,
+                 unsigned long long *__restrict__ hist_v)
+{
+    __shared__ unsigned int sh_d[AEB_NBINS];
+    __shared__ unsigned int sh_v[AEB_NBINS];
+    __shared__ RedPartial sh_p[kRedWarps];
+    for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
+        sh_d[j] = 0u;
+        sh_v[j] = 0u;
+    }
+    __syncthreads();
+
+    const uint64_t lo = (uint64_t)blockIdx.x * chunk;
+    const uint64_t hi = (lo + chunk < n) ? lo + chunk : n;
+    RedPartial acc;
+    init_partial(acc);
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        const uint8_t s = st[i];
+        acc.steps += (unsigned long long)(long long)ns[i];
+        if (s == AEB_STOP) {
+            const double d = xr[i];
+            acc.n_stop++;
+            acc.sum_d += d;
+            acc.sumsq_d += d * d;
+            acc.min_d = fmin(acc.min_d, d);
+            acc.max_d = fmax(acc.max_d, d);
+            atomicAdd(&sh_d[bin_index(d, lo_d, inv_wd)], 1u);
+        } else if (s == AEB_CONTACT) {
+            const double v = vi[i];
+            acc.n_contact++;
+            acc.sum_v += v;
+            acc.sumsq_v += v * v;
+            acc.min_v = fmin(acc.min_v, v);
+            acc.max_v = fmax(acc.max_v, v);
+            atomicAdd(&sh_v[bin_index(v, lo_v, inv_wv)], 1u);
+        } else if (s == AEB_HORIZON) {
+            acc.n_horizon++;
+        } else {
+            acc.n_invalid++;
+        }
+    }
+    acc = block_combine(acc, sh_p);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    __syncthreads();
+    for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
+        if (sh_d[j]) atomicAdd(&hist_d[j], (unsigned long long)sh_d[j]);
+        if (sh_v[j]) atomicAdd(&hist_v[j], (unsigned long long)sh_v[j]);
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_final(const RedPartial *__restrict__ part, int g, uint64_t n, aeb_hist_spec h,
+               aeb_stats *__restrict__ out)
+{
+    __shared__ RedPartial sh_p[kRedWarps];
+    RedPartial acc;
+    init_partial(acc);
+    for (int j = threadIdx.x; j < g; j += kRedThreads) add_partial(acc, part[j]);
+    acc = block_combine(acc, sh_p);
+    if (threadIdx.x == 0) {
+        out->n = n;
+        out->n_stop = acc.n_stop;
+        out->n_contact = acc.n_contact;
+        out->n_horizon = acc.n_horizon;
+        out->n_invalid = acc.n_invalid;
+        out->steps = acc.steps;
+        out->sum_d = acc.sum_d;
+        out->sumsq_d = acc.sumsq_d;
+        out->min_d = acc.min_d;
+        out->max_d = acc.max_d;
+        out->sum_v = acc.sum_v;
+        out->sumsq_v = acc.sumsq_v;
+        out->min_v = acc.min_v;
+        out->max_v = acc.max_v;
+        out->lo_d = h.lo_d;
+        out->w_d = h.w_d;
+        out->lo_v = h.lo_v;
+        out->w_v = h.w_v;
+    }
+}
+
+}  // namespace
+
+int reduce_blocks_for(uint64_t n)
+{
+    uint64_t g = (n + 8191) / 8192;
+    if (g < 1) g = 1;
+    if (g > 1024) g = 1024;
+    return (int)g;
+}
+
+cudaError_t launch_reduce(const uint8_t *status, const double *x_ref, const double *v_imp,
+                          const int32_t *n_steps, uint64_t n, const aeb_hist_spec &h,
+                          RedPartial *partials, aeb_stats *stats, cudaStream_t s)
+{
+    const int g = reduce_blocks_for(n);
+    const uint64_t chunk = (n + (uint64_t)g - 1) / (uint64_t)g;
+    cudaError_t e = cudaMemsetAsync(stats->hist_d, 0, 2 * sizeof(uint64_t) * AEB_NBINS, s);
+    if (e != cudaSuccess) return e;
+    k_reduce_partial<<<g, kRedThreads, 0, s>>>(
+        status, x_ref, v_imp, n_steps, n, chunk, h.lo_d, 1.0 / h.w_d, h.lo_v, 1.0 / h.w_v,
+        partials, reinterpret_cast<unsigned long long *>(stats->hist_d),
+        reinterpret_cast<unsigned long long *>(stats->hist_v));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, kRedThreads, 0, s>>>(partials, g, n, h, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace aeb

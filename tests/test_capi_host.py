@@ -1,0 +1,134 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every function ``include/aeb.h`` declares, its ctypes
+mirrors match the header's layouts, invalid arguments are rejected before any
+device work, and the host sampler reproduces the oracle's sampler bit for bit
+(Sec. IV-C: CPU and GPU runs consume identical parameter sets)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import aeb_inputs as ai
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aeb.h")
+
+
+@pytest.fixture(scope="module")
+def aeb():
+    import paper_2604_27193_gb300 as aeb
+    aeb.build()
+    return aeb
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(aeb_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(aeb):
+    names = declared_functions()
+    assert {"aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate"} <= set(names)
+    L = C.CDLL(aeb._build.LIB)
+    for n in names:
+        assert hasattr(L, n), n
+    assert aeb.lib().aeb_abi_version() == 1
+
+
+def test_struct_layouts_match_header(aeb, tmp_path):
+    probe = tmp_path / "probe.c"
+    structs = {"aeb_model": aeb.Model, "aeb_dist": aeb.Dist, "aeb_scenario": aeb.Scenario,
+               "aeb_params": aeb.Params, "aeb_outputs": aeb.Outputs,
+               "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    probe.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(probe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def _cols(n):
+    return {f: np.zeros(n, dtype=np.float64) for f in ai.FIELDS}
+
+
+def test_invalid_arguments_rejected_on_host(aeb):
+    L = aeb.lib()
+    m = aeb.model(ai.single_model())
+    p = aeb.params_struct(_cols(4))
+    o = aeb.outputs_struct(None)
+    bad = []
+    for field, val in (("dt", 0.0), ("dt", float("nan")), ("t_max", -1.0), ("wheelbase", 0.0),
+                       ("cap_mode", 7), ("trigger", 3), ("lead", 2), ("reserved", 1),
+                       ("g", float("inf"))):
+        mm = aeb.model(ai.single_model())
+        setattr(mm, field, val)
+        bad.append(mm)
+    mm = aeb.model(ai.single_model())
+    mm.dt, mm.t_max = 1e-9, 10.0  # 1e10 steps
+    bad.append(mm)
+    for mm in bad:
+        assert L.aeb_rollout(C.byref(mm), C.byref(p), 4, 0, C.byref(o), None) == aeb.EINVAL
+        assert L.aeb_last_error()
+    assert L.aeb_rollout(C.byref(m), C.byref(p), 4, 5, C.byref(o), None) == aeb.EINVAL
+    assert L.aeb_rollout(C.byref(m), None, 4, 0, C.byref(o), None) == aeb.EINVAL
+    p2 = aeb.params_struct(_cols(4))
+    p2.mu = 0
+    assert L.aeb_rollout(C.byref(m), C.byref(p2), 4, 0, C.byref(o), None) == aeb.EINVAL
+    p3 = aeb.params_struct(_cols(4))
+    p3.v0 = p3.v0 + 4
+    assert L.aeb_rollout(C.byref(m), C.byref(p3), 4, 0, C.byref(o), None) == aeb.EINVAL
+    # n == 0 is a no-op that never touches a device
+    assert L.aeb_rollout(C.byref(m), C.byref(p), 0, 0, C.byref(o), None) == aeb.OK
+    h = aeb.hist_spec(w_d=0.1)
+    assert L.aeb_reduce(C.byref(o), 0, C.byref(h), 8, None) == aeb.EINVAL
+    h = aeb.hist_spec()
+    assert L.aeb_reduce(C.byref(o), 5, C.byref(h), 8, None) == aeb.EINVAL  # NULL columns
+
+
+def test_sampler_matches_oracle_bitwise(aeb, oracle_mod):
+    """aeb_sample_params and the oracle's sampler are separate implementations
+    of the same definition; on the same host they must agree in every bit."""
+    cases = [(ai.single_model(), ai.single_scenario(seed=0), 0, 5000),
+             (ai.paper_model(), ai.paper_scenario(seed=3), 123456789, 3000)]
+    for sc, _n in ai.grid_scenarios()[:3]:
+        cases.append((ai.single_model(), sc, 7, 1000))
+    for m, sc, first, n in cases:
+        got = aeb.aeb_sample_params(m, sc, first, n, n_threads=3)
+        exp = oracle_mod.sample(m, sc, first, n)
+        for f in ai.FIELDS:
+            assert np.array_equal(got[f].view(np.uint64), exp[f].view(np.uint64)), f
+
+
+def test_sampler_thread_count_invariance(aeb):
+    m, sc = ai.single_model(), ai.single_scenario(seed=5)
+    a = aeb.aeb_sample_params(m, sc, 0, 20000, n_threads=1)
+    b = aeb.aeb_sample_params(m, sc, 0, 20000, n_threads=7)
+    c = aeb.aeb_sample_params(m, sc, 0, 20000, n_threads=0)
+    for f in ai.FIELDS:
+        assert np.array_equal(a[f], b[f]) and np.array_equal(a[f], c[f])
+
+
+def test_sampler_rejects_bad_distributions(aeb):
+    m = ai.single_model()
+    for bad in (ai.Dist(9, 0, 1), ai.Dist(ai.UNIFORM, float("nan"), 1.0),
+                ai.Dist(ai.NORMAL, 0.0, 1.0, 2.0, 1.0)):
+        sc = ai.replace(ai.single_scenario(), mu=bad)
+        with pytest.raises(aeb.AebError) as e:
+            aeb.aeb_sample_params(m, sc, 0, 10)
+        assert e.value.code == aeb.EINVAL
+    assert aeb.aeb_sample_params(m, ai.single_scenario(), 0, 0)["v0"].size == 0

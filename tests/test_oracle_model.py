@@ -208,6 +208,7 @@ def test_ttc_trigger_step(oracle_mod):
     m0 = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=-1.0)
     o3 = oracle_mod.rollout(m0, one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, 0.0)]))
     assert o3["status"][0] == 1 and abs(o3["v_imp"][0] - v0) < 1e-9
+    assert o3["n_onset"][0] == -1
 
 
 # ---------------------------------------------------------------------------
@@ -322,11 +323,11 @@ def test_ttc_trigger_step_random(oracle_mod):
         if D > d0 - 0.5:
             continue
         rows.append((v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, noise, thr))
-        expect.append(D)
-    for row, D in zip(rows, expect):
+        expect.append((D, math.ceil(q) + nd))
+    for row, (D, nb) in zip(rows, expect):
         m = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=row[9])
         o = oracle_mod.rollout(m, one([row[:9]]))
-        assert o["status"][0] == 0
+        assert o["status"][0] == 0 and o["n_onset"][0] == nb
         assert abs(o["x_ref"][0] - D) <= r * dt * dt / 8 + 1e-8, (row, D, o["x_ref"][0])
 
 

@@ -1,0 +1,280 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle on the same
+seeded inputs.
+
+  * AEB_FP64_PLAIN must equal the oracle in every bit of every output
+    (Sec. V-D / VI-A: maximum deviation 0.000000 m between CPU and GPU).
+  * AEB_FP32_COMP must stay within the stated tolerances:
+      - stopped in both: |x_ref - x_ref64| <= 1e-5 x_ref64 (relative);
+      - stop/contact flag may differ only where the path that stopped has
+        |d0 - x_ref| < 1e-3 m; such samples are counted;
+      - TTC trigger: the onset step may differ (the trigger is a threshold on
+        a state the two precisions carry with different rounding); such
+        samples are counted and reported, the others meet the bounds above;
+      - stopped: t_end within 1e-6 s + 1e-6 relative;
+      - contact: the contact instant and speed are as well conditioned as the
+        position allows, so the bound is the position bound carried through
+        the kinematics: |dt_end| v_imp <= 1e-5 d0 and
+        |dv_imp| v_imp <= r_max 1e-5 d0 (r_max = 10 m/s^2 bounds |dv/dt|);
+      - horizon: t_end identical.
+  * aeb_reduce: integer counts and histograms exact, extremes exact, sums
+    within n * 2^-52 * sum|x| of the exactly rounded sum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import aeb_inputs as ai
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def aeb():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2604_27193_gb300 as aeb
+    aeb.build()
+    aeb.lib()
+    return aeb
+
+
+def gpu_rollout(aeb, m, params, precision):
+    n = len(params["v0"])
+    P = {f: torch.from_numpy(np.ascontiguousarray(params[f])).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(max(n, 1))
+    aeb.aeb_rollout(m, P, n, precision, O)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy()[:n] for k, v in O.items()}
+
+
+def bits_equal(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    if a.dtype == np.float64:
+        return np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    return np.array_equal(a, b)
+
+
+def assert_bit_exact(got, exp):
+    for k in ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset"):
+        if not bits_equal(got[k], exp[k]):
+            bad = np.nonzero(got[k].view(np.uint64) != exp[k].view(np.uint64)
+                             if got[k].dtype == np.float64 else got[k] != exp[k])[0]
+            i = bad[0]
+            raise AssertionError(f"{k}: {len(bad)} mismatches, first at {i}: "
+                                 f"gpu {got[k][i]!r} oracle {exp[k][i]!r}")
+
+
+FP64_CASES = {
+    "single_scenario": (ai.single_model(), ai.single_scenario(seed=0), 10_000),
+    "paper_preset": (ai.paper_model(), ai.paper_scenario(seed=1), 4_000),
+    "ttc_1s": (ai.ttc_model(thr=1.0), ai.single_scenario(seed=2), 3_000),
+    "ttc_2.5s": (ai.ttc_model(thr=2.5), ai.single_scenario(seed=3), 3_000),
+    "lumped_lead": (ai.replace(ai.single_model(), cap_mode=ai.CAP_LUMPED),
+                    ai.single_scenario(seed=4), 3_000),
+    "per_axle_no_lead": (ai.replace(ai.single_model(), lead=0), ai.single_scenario(seed=5), 3_000),
+    "coarse_dt_20ms": (ai.single_model(dt=0.02), ai.single_scenario(seed=6), 3_000),
+    "fine_dt_0.1ms": (ai.single_model(dt=1e-4), ai.single_scenario(seed=7), 300),
+    "short_horizon": (ai.replace(ai.single_model(), t_max=1.5), ai.single_scenario(seed=8), 2_000),
+}
+
+
+@pytest.mark.parametrize("name", list(FP64_CASES))
+def test_fp64_bit_exact(aeb, oracle_mod, name):
+    m, sc, n = FP64_CASES[name]
+    p = ai.draw_params(m, sc, n)
+    exp = oracle_mod.rollout(m, p, threads=8)
+    got = gpu_rollout(aeb, m, p, aeb.FP64_PLAIN)
+    assert_bit_exact(got, exp)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 257, 1031, 4099])
+def test_fp64_ragged_sizes(aeb, oracle_mod, n):
+    m = ai.single_model()
+    p = ai.draw_params(m, ai.single_scenario(seed=n), n)
+    assert_bit_exact(gpu_rollout(aeb, m, p, aeb.FP64_PLAIN), oracle_mod.rollout(m, p))
+
+
+@pytest.mark.parametrize("lead,trigger", [(1, 0), (0, 0), (1, 1)])
+def test_edge_cases_both_precisions(aeb, oracle_mod, lead, trigger):
+    m = ai.replace(ai.single_model(), lead=lead, trigger=trigger, ttc_thr=2.0)
+    p = ai.edge_params(m)
+    exp = oracle_mod.rollout(m, p)
+    assert_bit_exact(gpu_rollout(aeb, m, p, aeb.FP64_PLAIN), exp)
+    got = gpu_rollout(aeb, m, p, aeb.FP32_COMP)
+    assert np.array_equal(got["status"], exp["status"])
+    inv = exp["status"] == 255
+    assert np.all(np.isnan(got["x_ref"][inv])) and np.all(got["n_steps"][inv] == 0)
+    ok = ~inv
+    assert np.allclose(got["x_ref"][ok], exp["x_ref"][ok], rtol=1e-5, atol=1e-7)
+
+
+def test_zero_samples_and_tiny_horizon(aeb, oracle_mod):
+    m = ai.replace(ai.single_model(), t_max=0.0)
+    p = ai.draw_params(m, ai.single_scenario(), 50)
+    exp = oracle_mod.rollout(m, p)
+    assert np.all(exp["status"] == 2)
+    assert_bit_exact(gpu_rollout(aeb, m, p, aeb.FP64_PLAIN), exp)
+    P = {f: torch.zeros(1, dtype=torch.float64, device="cuda") for f in ai.FIELDS}
+    aeb.aeb_rollout(ai.single_model(), P, 0, aeb.FP64_PLAIN, aeb.alloc_outputs(1))
+
+
+def fp32_report(m, got, exp):
+    """Compare FP32-compensated outputs with the binary64 ones; return counts
+    of tolerated disagreements and the worst errors, asserting the bounds."""
+    s32, s64 = got["status"], exp["status"]
+    d0 = None
+    on_diff = got["n_onset"] != exp["n_onset"]
+    if m.trigger == ai.TRIGGER_IMMEDIATE:
+        assert not np.any(on_diff), "onset step must match in immediate mode"
+    flag_diff = (s32 != s64) & ~on_diff
+    rep = {"n": len(s32), "onset_disagree": int(on_diff.sum()), "flag_disagree": int(flag_diff.sum())}
+    if flag_diff.any():
+        # whichever path stopped must have stopped within 1e-3 m of the lead
+        idx = np.nonzero(flag_diff)[0]
+        stopped_gap = np.where(s64[idx] == 0, exp["gap"][idx], got["gap"][idx])
+        assert np.all(np.abs(stopped_gap) < 1e-3), stopped_gap
+    same = (s32 == s64) & ~on_diff
+    st = same & (s64 == 0)
+    rel = np.abs(got["x_ref"][st] - exp["x_ref"][st]) / np.maximum(np.abs(exp["x_ref"][st]), 1e-3)
+    rep["x_ref_rel_max"] = float(rel.max()) if rel.size else 0.0
+    rep["x_ref_rel_mean"] = float(rel.mean()) if rel.size else 0.0
+    assert rep["x_ref_rel_max"] <= 1e-5, rep
+    ct = same & (s64 == 1)
+    if ct.any():
+        vi = exp["v_imp"][ct]
+        d0 = exp["x_ref"][ct]
+        dv = np.abs(got["v_imp"][ct] - vi)
+        dtc = np.abs(got["t_end"][ct] - exp["t_end"][ct])
+        rep["v_imp_abs_max"] = float(dv.max())
+        rep["contact_dt_x_v_over_d0_max"] = float((dtc * vi / d0).max())
+        rep["contact_dv_x_v_over_d0_max"] = float((dv * vi / d0).max())
+        assert np.all(dtc * vi <= 1e-5 * d0), rep
+        assert np.all(dv * vi <= 10.0 * 1e-5 * d0), rep
+    sp = same & (s64 == 0)
+    dts = np.abs(got["t_end"][sp] - exp["t_end"][sp])
+    rep["stop_t_end_abs_max"] = float(dts.max()) if dts.size else 0.0
+    assert np.all(dts <= 1e-6 + 1e-6 * exp["t_end"][sp]), rep
+    hz = same & (s64 == 2)
+    assert np.array_equal(got["t_end"][hz], exp["t_end"][hz])
+    return rep
+
+
+def with_gap(out, p, lead):
+    out = dict(out)
+    out["gap"] = (p["d0"] - out["x_ref"]) if lead else np.full(len(out["x_ref"]), np.inf)
+    return out
+
+
+FP32_CASES = {
+    "single_scenario": (ai.single_model(), ai.single_scenario(seed=10), 20_000),
+    "paper_preset": (ai.paper_model(), ai.paper_scenario(seed=11), 10_000),
+    "single_scenario_dt_0.1ms": (ai.single_model(dt=1e-4), ai.single_scenario(seed=12), 400),
+    "ttc_2s": (ai.ttc_model(thr=2.0), ai.single_scenario(seed=13), 10_000),
+    "grid_scenario": (ai.single_model(), ai.grid_scenarios()[1234][0], 5_000),
+}
+
+
+@pytest.mark.parametrize("name", list(FP32_CASES))
+def test_fp32_comp_within_tolerance(aeb, oracle_mod, name):
+    m, sc, n = FP32_CASES[name]
+    p = ai.draw_params(m, sc, n)
+    exp = with_gap(oracle_mod.rollout(m, p, threads=8), p, m.lead)
+    got = with_gap(gpu_rollout(aeb, m, p, aeb.FP32_COMP), p, m.lead)
+    rep = fp32_report(m, got, exp)
+    print(name, rep)
+    if m.trigger == ai.TRIGGER_TTC:
+        assert rep["onset_disagree"] <= max(3, 1e-3 * n), rep
+
+
+def test_reduce_against_oracle(aeb, oracle_mod):
+    m = ai.single_model()
+    p = ai.concat_params([ai.draw_params(m, ai.single_scenario(seed=20), 12_345),
+                          ai.edge_params(m)])
+    n = len(p["v0"])
+    exp_out = oracle_mod.rollout(m, p, threads=8)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n)
+    aeb.aeb_rollout(m, P, n, aeb.FP64_PLAIN, O)
+    for spec in ((0.0, 0.125, 0.0, 1 / 64), (20.0, 0.0625, -1.0, 0.25)):
+        S = aeb.alloc_stats()
+        aeb.aeb_reduce(O, n, aeb.hist_spec(*spec), S)
+        st = aeb.stats_from_buffer(S)
+        ex = oracle_mod.reduce(exp_out, spec[0], spec[1], spec[2], spec[3], 4096)
+        for k in ("n", "n_stop", "n_contact", "n_horizon", "n_invalid", "steps",
+                  "min_d", "max_d", "min_v", "max_v"):
+            assert getattr(st, k) == getattr(ex, k), k
+        assert np.array_equal(np.frombuffer(bytes(st.hist_d), np.uint64), ex.hist_d)
+        assert np.array_equal(np.frombuffer(bytes(st.hist_v), np.uint64), ex.hist_v)
+        d = exp_out["x_ref"][exp_out["status"] == 0]
+        v = exp_out["v_imp"][exp_out["status"] == 1]
+        for got, vals in ((st.sum_d, d), (st.sumsq_d, d * d), (st.sum_v, v), (st.sumsq_v, v * v)):
+            assert abs(got - math.fsum(vals)) <= len(vals) * 2.3e-16 * math.fsum(np.abs(vals))
+
+
+def test_reduce_empty(aeb):
+    O = aeb.alloc_outputs(1)
+    S = aeb.alloc_stats()
+    aeb.aeb_reduce(O, 0, aeb.hist_spec(), S)
+    st = aeb.stats_from_buffer(S)
+    assert st.n == 0 and st.n_stop == 0 and st.min_d == math.inf and st.max_d == -math.inf
+    assert sum(st.hist_d) == 0
+
+
+def test_deterministic_repeats(aeb):
+    m = ai.single_model()
+    n = 50_000
+    p = ai.draw_params(m, ai.single_scenario(seed=30), n)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    res = []
+    for _ in range(2):
+        O = aeb.alloc_outputs(n)
+        aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+        S = aeb.alloc_stats()
+        aeb.aeb_reduce(O, n, aeb.hist_spec(), S)
+        res.append((O, bytes(S.cpu().numpy())))
+    for k in res[0][0]:
+        assert torch.equal(res[0][0][k], res[1][0][k]), k
+    assert res[0][1] == res[1][1]
+
+
+def test_evaluate_host_path(aeb, oracle_mod):
+    """aeb_evaluate (host buffers in, host stats out) equals the device calls."""
+    m = ai.single_model()
+    n = 7_777
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=40), 0, n)
+    host_out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in aeb.OUTPUTS}
+    st = aeb.aeb_evaluate(m, p, n, aeb.FP64_PLAIN, aeb.hist_spec(), host_out=host_out)
+    exp = oracle_mod.rollout(m, p, threads=8)
+    assert_bit_exact(host_out, exp)
+    ex = oracle_mod.reduce(exp)
+    assert (st.n_stop, st.n_contact, st.n_horizon) == (ex.n_stop, ex.n_contact, ex.n_horizon)
+    assert np.array_equal(np.frombuffer(bytes(st.hist_d), np.uint64), ex.hist_d)
+    st2 = aeb.aeb_evaluate(m, p, n, aeb.FP64_PLAIN, aeb.hist_spec())
+    assert bytes(st2) == bytes(st)
+
+
+def test_full_size_sampled(aeb, oracle_mod):
+    """The single-scenario workload at N = 1e7 in the benchmark's launch
+    configuration: sampled outputs against the oracle, and invariants over
+    every sample."""
+    m = ai.single_model()
+    n = 10_000_000
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=0), 0, n)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n)
+    aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+    S = aeb.alloc_stats()
+    aeb.aeb_reduce(O, n, aeb.hist_spec(), S)
+    st = aeb.stats_from_buffer(S)
+    got = {k: v.cpu().numpy() for k, v in O.items()}
+    assert st.n == n and st.n_stop + st.n_contact + st.n_horizon + st.n_invalid == n
+    assert st.steps == int(got["n_steps"].astype(np.int64).sum())
+    assert np.all(got["n_steps"] >= 1)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 3000), [0, 1, n - 2, n - 1]]))
+    sub = {f: p[f][idx] for f in ai.FIELDS}
+    exp = with_gap(oracle_mod.rollout(m, sub, threads=8), sub, 1)
+    g = with_gap({k: v[idx] for k, v in got.items()}, sub, 1)
+    fp32_report(m, g, exp)
