@@ -216,6 +216,28 @@ aeb_status aeb_reduce(const aeb_outputs *out, uint64_t n, const aeb_hist_spec *h
                       aeb_stats *stats, void *stream);
 
 /*
+ * aeb_reduce_noalloc -- aeb_reduce without any device allocation, for callers
+ * that must not allocate once running (a real-time loop whose rules forbid
+ * allocation after start-up, or a process whose device memory is already held
+ * in full by another allocator).  The paper has no counterpart; this is a
+ * deployment variant of aeb_reduce.
+ *   Same arguments, ordering and results as aeb_reduce, for
+ *   n <= AEB_REDUCE_NOALLOC_MAX_N samples; larger n is rejected with
+ *   AEB_EINVAL and a message naming the limit.
+ *   Scratch: a fixed array of per-block partial sums compiled into the library
+ *   (26.6 KB on every GPU that loads it, held until the process exits).  All
+ *   calls share it, so calls whose GPU work overlaps (for example on two
+ *   streams) race and must be serialised by the caller.  Each call overwrites
+ *   the partials it reads and clears the histogram of `stats` first.
+ *   The first call on a device looks up the array's device address (no
+ *   allocation); make that first call before any stream capture.
+ * Asynchronous.  Calls no cudaMalloc, cudaFree or allocating routine.
+ */
+#define AEB_REDUCE_NOALLOC_MAX_N 2097152u
+aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n, const aeb_hist_spec *hist,
+                              aeb_stats *stats, void *stream);
+
+/*
  * aeb_evaluate -- the whole path from host buffers: copy the parameter columns
  * to device buffers owned by the library, roll out, reduce, copy the stats
  * (and the requested per-sample outputs) back, and wait for the stream.

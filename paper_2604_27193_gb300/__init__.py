@@ -212,6 +212,20 @@ def aeb_reduce(out: dict, n: int, hist: HistSpec, stats_dev, stream=None):
     _check(lib().aeb_reduce(C.byref(os_), n, C.byref(hist), _ptr(stats_dev), _stream(stream)))
 
 
+REDUCE_NOALLOC_MAX_N = 2097152
+
+
+def aeb_reduce_noalloc(out: dict, n: int, hist: HistSpec, stats_dev, stream=None):
+    """aeb_reduce without device allocation (fixed library scratch; at most
+    REDUCE_NOALLOC_MAX_N samples; concurrent calls must not overlap)."""
+    L = lib()
+    fn = L.aeb_reduce_noalloc
+    fn.argtypes = [C.POINTER(Outputs), C.c_uint64, C.POINTER(HistSpec), C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int32
+    os_ = outputs_struct(out)
+    _check(fn(C.byref(os_), n, C.byref(hist), _ptr(stats_dev), _stream(stream)))
+
+
 def aeb_evaluate(m, params_host: dict, n: int, precision: int, hist: HistSpec,
                  host_out: dict | None = None, stream=None) -> Stats:
     """Whole path from host columns; returns the stats (synchronous)."""

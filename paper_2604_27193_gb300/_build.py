@@ -25,6 +25,7 @@ CU_SOURCES = {
     "rollout_fp64.cu": ["-fmad=false"],
     "rollout_fp32.cu": [],
     "reduce.cu": [],
+    "reduce_noalloc.cu": [],
 }
 CPP_SOURCES = ["capi.cpp", "sampler.cpp"]
 HEADERS = ["aeb_internal.h", "rollout_common.cuh", "host_util.h"]
