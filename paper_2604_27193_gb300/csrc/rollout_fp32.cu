@@ -1,27 +1,49 @@
 // rollout_fp32.cu -- binary32 rollout kernel with compensated state.
 //
 // The RK4 stages of Eq. 7-9 (Sec. IV-D) run in binary32 with fused
-// multiply-add.  Position and speed are carried as unevaluated double-float
-// sums (hi + lo): each step's increment is added with Fast2Sum and its rounding
-// error kept in lo, so 1e4-1e5 increments of 1e-3-1e-4 relative size do not
-// lose the ~1e-7 relative precision of a binary32 stage.  The speed pair is
-// renormalised every step because the stages read its high word.  The contact test compares the
-// double-float position with a double-float d0, and the TTC trigger margin
-// (gap - thr v) is formed with exact product and sum error terms.  Binary64 is
-// used only once per sample: the brake-onset step (the same integer rule as the
-// binary64 path, so the onset step is always identical) and the linear
-// stop/contact refinement of the last step from the hi + lo pairs.
+// multiply-add.  Speed and the gap to the lead (g = d0 - x) are carried as
+// unevaluated double-float pairs (hi + lo): each step's increment is added with
+// Fast2Sum and its rounding error kept in lo, so 1e4-1e5 increments of
+// 1e-3-1e-4 relative size do not lose the ~1e-7 relative precision of a
+// binary32 stage.  Each update is Fast2Sum of (hi, lo + increment), which keeps
+// the pair normalised (|lo| <= ulp(hi)/2): the stages read the speed's high word
+// (with lo left to grow, a nearly constant increment leaves the same rounding
+// residual every step and the stages see a biased speed), and a slow car's step
+// can be far below half an ulp of the gap.  Contact is g <= 0 on the pair; the TTC margin
+// (g + noise) - thr v is formed with the exact error of thr v.
 //
-// The actuator lag (Eq. 6) is linear with the command u held over the step.
-// The lane carries the deviation e = a - u instead of a: RK4's stage values
-// are u + p_j e with p1 = 1, p2 = 1 - z/2, p3 = 1 - z/2 + z^2/4,
-// p4 = 1 - z + z^2/2 - z^3/4 (z = dt / tau), and the step maps e to
-// e - mP e with mP = z - z^2/2 + z^3/6 - z^4/24; this is what the four RK4
-// stages of Eq. 6 evaluate.  Carried as a, the state would stall about
-// ulp(a) / (2 z) short of the command in binary32; carried as e it decays with
-// full relative precision.  When the command switches from 0 to a_cmd at the
-// onset step, e drops by a_cmd.  tau = 0 (instantaneous actuator) is the case
-// p_j = 0, mP = 1.
+// Actuator (Eq. 6).  The lag is linear with the command u held over a step, so
+// the lane carries e = a - u: RK4's stage values are u + p_j e with p1 = 1,
+// p2 = 1 - z/2, p3 = 1 - z/2 + z^2/4, p4 = 1 - z + z^2/2 - z^3/4 (z = dt/tau),
+// and one step maps e to e - mP e with mP = z - z^2/2 + z^3/6 - z^4/24: the
+// four RK4 stages of Eq. 6, written so that the decay keeps binary32 relative
+// precision (a binary32 `a` would stall ~ulp(a)/(2z) short of the command).
+// tau = 0 (instantaneous actuator) is p_j = 0, mP = 1.
+//
+// Realised deceleration (Eq. 4-5 / per-axle caps).  r(D) is the minimum of the
+// lines D, f0 + f1 D, r0 + r1 D and mu g cos(theta) (Eq. 5 as printed: D and
+// mu g / (1 + mu h/L)).  After brake onset the demand D = -a only grows, so the
+// lane keeps the line that is the minimum at the step's smallest demand and the
+// threshold on e beyond which the step's largest demand would pass the next
+// breakpoint.  Inside a piece every stage costs one FMA:
+//     r_j + g sin(theta) = C - (slope e) p_j,  C = intercept - slope u + g sin(theta).
+// A step that crosses a breakpoint evaluates the full minimum for its four
+// stages, then moves to the next piece.
+//
+// Binary64 runs at 1/64 of the binary32 rate on GB300, so it is kept out of the
+// step loop and done at full SIMT width: when a warp claims a tile of 64
+// samples, all 32 lanes prepare the tile's binary32 constants together into
+// shared memory (brake-onset step by the binary64 rule, hi/lo splits of v0 and
+// d0, drag and cap coefficients, actuator multipliers).  Lanes whose rollout
+// ends refill from that tile.  The binary64 refinement of the last step (linear
+// stop/contact interpolation from the hi + lo pairs) is also batched: an ending
+// lane queues its terminal state in the warp's shared slab, and the warp refines
+// 32 queued rollouts at once.
+//
+// Steps that need more than the piece formula take a slow path: the brake-onset
+// step, the last step before the horizon, and a step that crosses a breakpoint.
+// The next such step is kept per lane, so the fast path tests one integer and
+// one float per step.
 #include <climits>
 
 #include "rollout_common.cuh"
@@ -29,30 +51,136 @@
 namespace aeb {
 namespace {
 
+constexpr int kTile = 64;      // samples per warp tile
+constexpr int kWarps = 4;      // warps per block
+constexpr int kThreads = 32 * kWarps;
+#ifndef AEB_FP32_MIN_BLOCKS
+#define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
+#endif
+
+// prepared per-sample record, stored field-major in shared memory
+enum {
+    R_V0H, R_V0L, R_D0H, R_D0L, R_GS, R_K, R_F0, R_F1, R_R0, R_R1, R_MG,
+    R_NP1, R_NP2, R_NP3, R_NP4, R_P4, R_NMP, R_NZ, R_NF  // float fields
+};
+enum { R_NDELAY, R_KIND, R_NI };  // int fields
+enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
+constexpr int kTileWords = (R_NF + R_NI) * kTile;
+
 struct ModelF32 {
-    float g, rho, area, hl, beta, phi_f;
     float dt, h6, nh2, nh6, ndt, acmd, thr_h, thr_l;
 };
 
-template <int CAP, bool LEAD, bool TTC>
+__device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
+
+// Prepare samples [start, start + cnt) of a tile into the warp's shared slab.
+template <bool LEAD, bool TTC>
+__device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P, uint64_t start,
+                                          int cnt, float *tf, int *ti)
+{
+    for (int j = threadIdx.x & 31; j < cnt; j += 32) {
+        const uint64_t i = start + j;
+        double f[AEB_NFIELDS];
+        load_fields(P, i, f);
+        int kind = K_RUN, nd = 0;
+        if (!sample_valid(f)) {
+            kind = K_INVALID;
+        } else {
+            nd = steps_to_reach_dev(f[kTdelay], M.dt);
+            if (LEAD && f[kD0] <= 0.0) kind = K_CONTACT0;
+            else if (f[kV0] <= 0.0) kind = K_STOP0;
+            else if (M.n_max == 0) kind = K_HORIZON0;
+        }
+        ti[R_NDELAY * kTile + j] = nd;
+        ti[R_KIND * kTile + j] = kind;
+        if (kind != K_RUN) continue;
+        const float v0h = __double2float_rn(f[kV0]);
+        const float d0h = __double2float_rn(f[kD0]);
+        tf[R_V0H * kTile + j] = v0h;
+        tf[R_V0L * kTile + j] = __double2float_rn(f[kV0] - (double)v0h);
+        tf[R_D0H * kTile + j] = d0h;
+        tf[R_D0L * kTile + j] = __double2float_rn(f[kD0] - (double)d0h);
+        tf[R_GS * kTile + j] = __double2float_rn(f[kGs]);
+        tf[R_K * kTile + j] = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
+        const double mu = f[kMu], mh = mu * M.hl;
+        if (M.cap_mode == AEB_CAP_LUMPED) {
+            tf[R_F0 * kTile + j] = finf();
+            tf[R_F1 * kTile + j] = 0.0f;
+            tf[R_R0 * kTile + j] = finf();
+            tf[R_R1 * kTile + j] = 0.0f;
+            tf[R_MG * kTile + j] = __double2float_rn((mu * M.g) / (1.0 + mh));
+        } else {
+            const double mg = mu * f[kGc], im = 1.0 / (1.0 - mh), ip = 1.0 / (1.0 + mh);
+            tf[R_F0 * kTile + j] = __double2float_rn((mg * M.phi_f) * im);
+            tf[R_F1 * kTile + j] = __double2float_rn((1.0 - M.beta) * im);
+            tf[R_R0 * kTile + j] = __double2float_rn((mg * (1.0 - M.phi_f)) * ip);
+            tf[R_R1 * kTile + j] = __double2float_rn(M.beta * ip);
+            tf[R_MG * kTile + j] = __double2float_rn(mg);
+        }
+        if (f[kTau] > 0.0) {
+            const double z = M.dt / f[kTau];
+            const double p4 = 1.0 - z + 0.5 * z * z - 0.25 * z * z * z;
+            tf[R_NP1 * kTile + j] = -1.0f;
+            tf[R_NP2 * kTile + j] = __double2float_rn(-(1.0 - 0.5 * z));
+            tf[R_NP3 * kTile + j] = __double2float_rn(-(1.0 - 0.5 * z + 0.25 * z * z));
+            tf[R_NP4 * kTile + j] = __double2float_rn(-p4);
+            tf[R_P4 * kTile + j] = __double2float_rn(p4);
+            tf[R_NMP * kTile + j] =
+                __double2float_rn(-(z * (1.0 + z * (-0.5 + z * (1.0 / 6.0 - z / 24.0)))));
+        } else {
+            tf[R_NP1 * kTile + j] = 0.0f;
+            tf[R_NP2 * kTile + j] = 0.0f;
+            tf[R_NP3 * kTile + j] = 0.0f;
+            tf[R_NP4 * kTile + j] = 0.0f;
+            tf[R_P4 * kTile + j] = 0.0f;
+            tf[R_NMP * kTile + j] = -1.0f;
+        }
+        tf[R_NZ * kTile + j] = TTC ? __double2float_rn(f[kNoise]) : 0.0f;
+    }
+}
+
+template <bool LEAD, bool TTC>
 struct Lane32 {
-    float xh, xl, vh, vl, e;
-    float d0h, d0l, gs, k;
-    float mg, nf1, f0, nr1, r0, cap;
-    float p1, p2, p3, p4, nmP;
-    float nzh, nzl;
-    int32_t n, n_b, n_delay;
+    float vh, vl, gh, gl, e;      // state: speed, gap d0 - x, actuator deviation a - u
+    float u, C, sp, eth;          // command, current piece of r(D)
+    float k, gs, f0, f1, r0, r1, mg;
+    float np1, np2, np3, np4, p4, nmP, nz;
+    int32_t n, ev, n_b, n_delay;  // step, next slow step, onset step, delay steps
     bool trig;
 
-    // -(dv/dt) = r + g sin(theta) + k v^2 for actuator state a (Eq. 4-5).
-    __device__ __forceinline__ float qacc(float vv, float aa) const
+    // Select the line of r(D) that is the minimum at demand D (ties: the
+    // flatter line, which stays the minimum to the right), its next breakpoint
+    // B, and the threshold on e beyond which a step's largest demand
+    // D4 = -(u + p4 e) exceeds B.
+    __device__ __forceinline__ void set_piece(float D)
     {
-        float r;
-        if (CAP == AEB_CAP_LUMPED)
-            r = fminf(-aa, cap);
-        else
-            r = fminf(fminf(-aa, mg), fminf(fmaf(nf1, aa, f0), fmaf(nr1, aa, r0)));
-        return fmaf(k * vv, vv, r + gs);
+        const float a_[4] = {0.0f, f0, r0, mg};
+        const float b_[4] = {1.0f, f1, r1, 0.0f};
+        float ab = 0.0f, bb = 1.0f, bv = D;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            const float vj = fmaf(b_[j], D, a_[j]);
+            if (vj < bv || (vj == bv && b_[j] < bb)) {
+                bv = vj;
+                ab = a_[j];
+                bb = b_[j];
+            }
+        }
+        float B = finf();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (b_[j] < bb) B = fminf(B, (a_[j] - ab) / (bb - b_[j]));
+        sp = bb;
+        C = (ab - bb * u) + gs;
+        eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
+    }
+
+    // r + g sin(theta) by the full minimum (slow steps)
+    __device__ __forceinline__ float rg_full(float np) const
+    {
+        const float D = -fmaf(-np, e, u);
+        const float r = fminf(fminf(D, mg), fminf(fmaf(f1, D, f0), fmaf(r1, D, r0)));
+        return r + gs;
     }
 
     __device__ __forceinline__ int32_t onset() const
@@ -60,169 +188,269 @@ struct Lane32 {
         return TTC ? (trig ? n_b : -1) : n_delay;
     }
 
-    __device__ __forceinline__ bool init(const ModelDev &M, const ModelF32 &F, const ParamsDev &P,
-                                         const OutDev &O, uint64_t i)
+    // Next step that must take the slow path: the onset step (if still ahead,
+    // possibly the current step) or the last step.
+    __device__ __forceinline__ void next_event(int32_t n_last)
     {
-        double f[AEB_NFIELDS];
-        load_fields(P, i, f);
-        if (!sample_valid(f)) {
-            const double nan = __longlong_as_double(0x7ff8000000000000ll);
-            store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
-            return true;
-        }
-        n_delay = steps_to_reach_dev(f[kTdelay], M.dt);
-        trig = !TTC;
-        n_b = n_delay;
-        const int32_t on = TTC ? -1 : n_delay;
-        const double d0 = f[kD0];
-        if (LEAD && d0 <= 0.0) {
-            store_out(O, i, AEB_CONTACT, 0.0, 0.0, f[kV0], 0.0, 0, on);
-            return true;
-        }
-        if (f[kV0] <= 0.0) {
-            store_out(O, i, AEB_STOP, 0.0, 0.0, 0.0, 0.0, 0, on);
-            return true;
-        }
-        if (M.n_max == 0) {
-            store_out(O, i, AEB_HORIZON, 0.0, 0.0, 0.0, 0.0, 0, on);
-            return true;
-        }
-        d0h = __double2float_rn(d0);
-        d0l = __double2float_rn(d0 - (double)d0h);
-        gs = __double2float_rn(f[kGs]);
-        k = ((F.rho * __double2float_rn(f[kCd])) * F.area) / (2.0f * __double2float_rn(f[kMass]));
-        const float mu = __double2float_rn(f[kMu]);
-        const float mh = mu * F.hl;
-        if (CAP == AEB_CAP_LUMPED) {
-            cap = (mu * F.g) / (1.0f + mh);
-        } else {
-            mg = mu * __double2float_rn(f[kGc]);
-            const float im = 1.0f / (1.0f - mh), ip = 1.0f / (1.0f + mh);
-            f0 = (mg * F.phi_f) * im;
-            nf1 = -(1.0f - F.beta) * im;
-            r0 = (mg * (1.0f - F.phi_f)) * ip;
-            nr1 = -F.beta * ip;
-        }
-        const float tau = __double2float_rn(f[kTau]);
-        if (f[kTau] > 0.0) {
-            const double z = M.dt / f[kTau];
-            p1 = 1.0f;
-            p2 = __double2float_rn(1.0 - 0.5 * z);
-            p3 = __double2float_rn(1.0 - 0.5 * z + 0.25 * z * z);
-            p4 = __double2float_rn(1.0 - z + 0.5 * z * z - 0.25 * z * z * z);
-            nmP = __double2float_rn(-(z * (1.0 + z * (-0.5 + z * (1.0 / 6.0 - z / 24.0)))));
-        } else {
-            p1 = p2 = p3 = p4 = 0.0f;
-            nmP = -1.0f;
-        }
-        if (TTC) {
-            nzh = __double2float_rn(f[kNoise]);
-            nzl = __double2float_rn(f[kNoise] - (double)nzh);
-        }
-        xh = 0.0f;
-        xl = 0.0f;
-        vh = __double2float_rn(f[kV0]);
-        vl = __double2float_rn(f[kV0] - (double)vh);
-        e = 0.0f;  // a = 0 and the command before onset is 0
-        n = 0;
-        return false;
+        ev = (trig && n_b >= n && n_b < n_last) ? n_b : n_last;
     }
 
-    __device__ __forceinline__ bool step(const ModelDev &M, const ModelF32 &F, const ParamsDev &P,
-                                         const OutDev &O, uint64_t i)
+    // Load sample `slot` of the warp's tile; true if it ended at once (stored).
+    __device__ __forceinline__ bool init(const ModelDev &M, const ParamsDev &P, const OutDev &O,
+                                         uint64_t i, int slot, const float *tf, const int *ti)
     {
-        if (TTC && !trig) {
-            // measured gap (d0 - x) + noise against thr * v, as double-float
-            const float s = d0h - xh;
-            const float bb = s - d0h;
-            const float es = (d0h - (s - bb)) + (-xh - bb);
-            const float p = F.thr_h * vh;
-            const float pe = fmaf(F.thr_h, vh, -p);
-            const float hi = s - p;
-            const float lo = ((es + (d0l - xl)) + (nzh + nzl)) - ((pe + F.thr_h * vl) + F.thr_l * vh);
-            if (hi + lo <= 0.0f) {
-                trig = true;
-                long long nb = (long long)n + n_delay;
-                n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
-            }
-        }
-        const bool on = trig && n >= n_b;
-        const float u = on ? F.acmd : 0.0f;
-        const float ee = (trig && n == n_b) ? e - F.acmd : e;  // command switches on
-        const float a1 = fmaf(ee, p1, u);
-        const float a2 = fmaf(ee, p2, u);
-        const float a3 = fmaf(ee, p3, u);
-        const float a4 = fmaf(ee, p4, u);
-        const float en = fmaf(nmP, ee, ee);
-
-        const float q1 = qacc(vh, a1);
-        const float v2 = fmaf(F.nh2, q1, vh);
-        const float q2 = qacc(v2, a2);
-        const float v3 = fmaf(F.nh2, q2, vh);
-        const float q3 = qacc(v3, a3);
-        const float v4 = fmaf(F.ndt, q3, vh);
-        const float q4 = qacc(v4, a4);
-
-        const float dv = F.nh6 * fmaf(2.0f, q2 + q3, q1 + q4);
-        const float dx = fmaf(F.dt, vl, F.h6 * fmaf(2.0f, v2 + v3, vh + v4));
-        // v: Fast2Sum of the increment, then renormalise so |vl| <= ulp(vh)/2.
-        // Without the renormalisation a nearly constant increment leaves the
-        // same rounding residual every step, vl grows linearly and the stages,
-        // which read vh, see a biased speed.
-        const float vs0 = vh + dv;
-        const float tv = vl + (dv - (vs0 - vh));
-        const float vs = vs0 + tv;
-        const float vln = tv - (vs - vs0);
-        // x: Fast2Sum only (no stage reads x)
-        const float xs = xh + dx;
-        const float xln = xl + (dx - (xs - xh));
-
-        const bool contact = LEAD && ((xs - d0h) + (xln - d0l) >= 0.0f);
-        const bool stop = vs <= 0.0f;
-        if (contact || stop || n + 1 >= M.n_max) {
-            const double x0 = (double)xh + (double)xl, x1 = (double)xs + (double)xln;
-            const double w0 = (double)vh + (double)vl, w1 = (double)vs + (double)vln;
-            const double dt = M.dt;
-            if (contact) {
-                const double d0 = __ldg(P.col[kD0] + i);
-                const double s = (d0 - x0) / (x1 - x0);
-                store_out(O, i, AEB_CONTACT, x1, d0, w0 + s * (w1 - w0), ((double)n + s) * dt,
-                          n + 1, onset());
-            } else if (stop) {
-                const double s = w0 / (w0 - w1);
-                store_out(O, i, AEB_STOP, x1, x0 + s * (x1 - x0), 0.0, ((double)n + s) * dt,
-                          n + 1, onset());
+        const int kind = ti[R_KIND * kTile + slot];
+        n_delay = ti[R_NDELAY * kTile + slot];
+        if (kind != K_RUN) {
+            const int32_t on = TTC ? -1 : n_delay;
+            if (kind == K_INVALID) {
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
+            } else if (kind == K_CONTACT0) {
+                store_out(O, i, AEB_CONTACT, 0.0, 0.0, __ldg(P.col[kV0] + i), 0.0, 0, on);
+            } else if (kind == K_STOP0) {
+                store_out(O, i, AEB_STOP, 0.0, 0.0, 0.0, 0.0, 0, on);
             } else {
-                store_out(O, i, AEB_HORIZON, x1, x1, 0.0, (double)(n + 1) * dt, n + 1, onset());
+                store_out(O, i, AEB_HORIZON, 0.0, 0.0, 0.0, 0.0, 0, on);
             }
             return true;
         }
-        xh = xs;
-        xl = xln;
-        vh = vs;
-        vl = vln;
-        e = en;
-        n = n + 1;
+        vh = tf[R_V0H * kTile + slot];
+        vl = tf[R_V0L * kTile + slot];
+        gh = tf[R_D0H * kTile + slot];
+        gl = tf[R_D0L * kTile + slot];
+        gs = tf[R_GS * kTile + slot];
+        k = tf[R_K * kTile + slot];
+        f0 = tf[R_F0 * kTile + slot];
+        f1 = tf[R_F1 * kTile + slot];
+        r0 = tf[R_R0 * kTile + slot];
+        r1 = tf[R_R1 * kTile + slot];
+        mg = tf[R_MG * kTile + slot];
+        np1 = tf[R_NP1 * kTile + slot];
+        np2 = tf[R_NP2 * kTile + slot];
+        np3 = tf[R_NP3 * kTile + slot];
+        np4 = tf[R_NP4 * kTile + slot];
+        p4 = tf[R_P4 * kTile + slot];
+        nmP = tf[R_NMP * kTile + slot];
+        nz = tf[R_NZ * kTile + slot];
+        e = 0.0f;  // a = 0 and the command is 0 before onset
+        u = 0.0f;
+        n = 0;
+        trig = !TTC;
+        n_b = TTC ? INT_MAX : n_delay;
+        next_event(M.n_max - 1);
+        set_piece(0.0f);
         return false;
     }
 };
 
-template <int CAP, bool LEAD, bool TTC>
-__global__ void __launch_bounds__(128) k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P,
-                                                      OutDev O, WorkDev W)
+// Terminal records waiting for the binary64 refinement, per warp, field-major.
+enum { B_G0H, B_G0L, B_G1H, B_G1L, B_W0H, B_W0L, B_W1H, B_W1L, B_NF };
+enum { B_IDXLO, B_IDXHI, B_STATUS, B_N1, B_ONSET, B_NI };
+constexpr int kBatchWords = (B_NF + B_NI) * 32;
+constexpr int kWarpWords = kTileWords + kBatchWords;
+constexpr size_t kSmemPerBlockAll = sizeof(float) * kWarpWords * kWarps;
+
+// Binary64 refinement of the last step for the warp's queued records, all 32
+// lanes at once (Sec. V-D termination; the refinement of the last step).
+__device__ __forceinline__ void flush_batch(const ModelDev &M, const ParamsDev &P,
+                                            const OutDev &O, const float *bf, const int *bi,
+                                            int count)
 {
-    rollout_driver<Lane32<CAP, LEAD, TTC>>(M, F, P, O, W);
+    __syncwarp();
+    const int j = threadIdx.x & 31;
+    if (j < count) {
+        const uint64_t i = (uint64_t)(uint32_t)bi[B_IDXLO * 32 + j] |
+                           ((uint64_t)(uint32_t)bi[B_IDXHI * 32 + j] << 32);
+        const int status = bi[B_STATUS * 32 + j];
+        const int32_t n1 = bi[B_N1 * 32 + j];
+        const int32_t on = bi[B_ONSET * 32 + j];
+        const double d0 = __ldg(P.col[kD0] + i);
+        const double x0 = d0 - ((double)bf[B_G0H * 32 + j] + (double)bf[B_G0L * 32 + j]);
+        const double x1 = d0 - ((double)bf[B_G1H * 32 + j] + (double)bf[B_G1L * 32 + j]);
+        const double w0 = (double)bf[B_W0H * 32 + j] + (double)bf[B_W0L * 32 + j];
+        const double w1 = (double)bf[B_W1H * 32 + j] + (double)bf[B_W1L * 32 + j];
+        const double n = (double)(n1 - 1);
+        if (status == AEB_CONTACT) {
+            const double s = (d0 - x0) / (x1 - x0);
+            store_out(O, i, AEB_CONTACT, x1, d0, w0 + s * (w1 - w0), (n + s) * M.dt, n1, on);
+        } else if (status == AEB_STOP) {
+            const double s = w0 / (w0 - w1);
+            store_out(O, i, AEB_STOP, x1, x0 + s * (x1 - x0), 0.0, (n + s) * M.dt, n1, on);
+        } else {
+            store_out(O, i, AEB_HORIZON, x1, x1, 0.0, (double)n1 * M.dt, n1, on);
+        }
+    }
+    __syncwarp();
+}
+
+// One warp walks tiles of kTile samples claimed from a global counter; see the
+// file comment.  No wait on other warps or on the host: the loop ends when the
+// tiles are used up and no lane holds a rollout.
+template <bool LEAD, bool TTC>
+__global__ void __launch_bounds__(kThreads, AEB_FP32_MIN_BLOCKS)
+k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
+{
+    extern __shared__ float smem[];
+    const unsigned lane = threadIdx.x & 31u;
+    float *tf = smem + (threadIdx.x >> 5) * kWarpWords;
+    int *ti = reinterpret_cast<int *>(tf + R_NF * kTile);
+    float *bf = tf + kTileWords;
+    int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
+    const int32_t n_last = M.n_max - 1;
+
+    uint64_t tile_start = 0;
+    int tile_cnt = 0, cursor = 0, bcount = 0;
+    bool dry = false;
+    Lane32<LEAD, TTC> L;
+    uint64_t idx = 0;
+    bool active = false;
+    unsigned need = kFull;
+    for (;;) {
+        if (need) {
+            while (need) {
+                if (cursor >= tile_cnt) {
+                    if (dry) {
+                        if ((need >> lane) & 1u) active = false;
+                        break;
+                    }
+                    unsigned long long t = 0;
+                    if (lane == 0) t = atomicAdd(W.counter, 1ull);
+                    t = __shfl_sync(kFull, t, 0);
+                    const uint64_t start = (uint64_t)t * kTile;
+                    if (start >= W.n) {
+                        dry = true;
+                        continue;
+                    }
+                    tile_start = start;
+                    tile_cnt = (int)((W.n - start < (uint64_t)kTile) ? W.n - start : kTile);
+                    cursor = 0;
+                    __syncwarp();  // every lane has read its record of the previous tile
+                    prep_tile<LEAD, TTC>(M, P, tile_start, tile_cnt, tf, ti);
+                    __syncwarp();
+                }
+                const unsigned rank = __popc(need & lanemask_lt());
+                const bool got = ((need >> lane) & 1u) && (int)rank < tile_cnt - cursor;
+                bool ended = false;
+                if (got) {
+                    const int slot = cursor + (int)rank;
+                    idx = tile_start + slot;
+                    active = true;
+                    ended = L.init(M, P, O, idx, slot, tf, ti);
+                }
+                const unsigned taken = __ballot_sync(kFull, got);
+                cursor += __popc(taken);
+                need = (need & ~taken) | __ballot_sync(kFull, ended);
+            }
+            if (!__any_sync(kFull, active)) {
+                flush_batch(M, P, O, bf, bi, bcount);
+                return;
+            }
+        }
+
+        // ---- one RK4 step (Sec. IV-D) ----
+        int status = -1;
+        float g1h = 0.0f, g1l = 0.0f, w1h = 0.0f, w1l = 0.0f;
+        if (active) {
+            if (TTC && !L.trig) {
+                // (g + noise) - thr v <= 0, with the exact rounding error of thr * vh
+                const float p = F.thr_h * L.vh;
+                const float pe = fmaf(F.thr_h, L.vh, -p);
+                const float hi = L.gh - p;
+                const float lo = (L.gl + L.nz) - (pe + fmaf(F.thr_h, L.vl, F.thr_l * L.vh));
+                if (hi + lo <= 0.0f) {
+                    L.trig = true;
+                    const long long nb = (long long)L.n + L.n_delay;
+                    L.n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
+                    L.ev = (L.n_b < n_last) ? L.n_b : n_last;
+                }
+            }
+            const bool slow = (L.n == L.ev) || (L.e < L.eth);
+            float q1, q2, q3, q4, v2, v3, v4;
+            if (!slow) {
+                const float S = L.sp * L.e;
+                q1 = fmaf(L.k * L.vh, L.vh, fmaf(S, L.np1, L.C));
+                v2 = fmaf(F.nh2, q1, L.vh);
+                q2 = fmaf(L.k * v2, v2, fmaf(S, L.np2, L.C));
+                v3 = fmaf(F.nh2, q2, L.vh);
+                q3 = fmaf(L.k * v3, v3, fmaf(S, L.np3, L.C));
+                v4 = fmaf(F.ndt, q3, L.vh);
+                q4 = fmaf(L.k * v4, v4, fmaf(S, L.np4, L.C));
+            } else {
+                if (L.n == L.n_b) {  // brake onset at the start of this step
+                    L.u = F.acmd;
+                    L.e = L.e - F.acmd;
+                }
+                q1 = fmaf(L.k * L.vh, L.vh, L.rg_full(L.np1));
+                v2 = fmaf(F.nh2, q1, L.vh);
+                q2 = fmaf(L.k * v2, v2, L.rg_full(L.np2));
+                v3 = fmaf(F.nh2, q2, L.vh);
+                q3 = fmaf(L.k * v3, v3, L.rg_full(L.np3));
+                v4 = fmaf(F.ndt, q3, L.vh);
+                q4 = fmaf(L.k * v4, v4, L.rg_full(L.np4));
+            }
+            const float dv = F.nh6 * fmaf(2.0f, q2 + q3, q1 + q4);
+            const float dx = fmaf(F.dt, L.vl, F.h6 * fmaf(2.0f, v2 + v3, L.vh + v4));
+            // compensated updates: Fast2Sum of (hi, lo + increment) keeps each
+            // pair normalised (|lo| <= ulp(hi) / 2)
+            const float tv = dv + L.vl;
+            w1h = L.vh + tv;
+            w1l = tv - (w1h - L.vh);
+            const float tg = L.gl - dx;
+            g1h = L.gh + tg;
+            g1l = tg - (g1h - L.gh);
+            const float en = fmaf(L.nmP, L.e, L.e);
+            if (LEAD && g1h <= 0.0f)
+                status = AEB_CONTACT;
+            else if (w1h <= 0.0f)
+                status = AEB_STOP;
+            else if (slow && L.n >= n_last)
+                status = AEB_HORIZON;
+            if (status < 0) {
+                L.vh = w1h;
+                L.vl = w1l;
+                L.gh = g1h;
+                L.gl = g1l;
+                L.e = en;
+                L.n = L.n + 1;
+                if (slow) {
+                    L.set_piece(-fmaf(-L.np1, L.e, L.u));
+                    L.next_event(n_last);
+                }
+            }
+        }
+        const unsigned endm = __ballot_sync(kFull, status >= 0);
+        if (endm) {
+            const int cnt = __popc(endm);
+            if (bcount + cnt > 32) {
+                flush_batch(M, P, O, bf, bi, bcount);
+                bcount = 0;
+            }
+            if (status >= 0) {
+                const int j = bcount + __popc(endm & lanemask_lt());
+                bf[B_G0H * 32 + j] = L.gh;
+                bf[B_G0L * 32 + j] = L.gl;
+                bf[B_G1H * 32 + j] = g1h;
+                bf[B_G1L * 32 + j] = g1l;
+                bf[B_W0H * 32 + j] = L.vh;
+                bf[B_W0L * 32 + j] = L.vl;
+                bf[B_W1H * 32 + j] = w1h;
+                bf[B_W1L * 32 + j] = w1l;
+                bi[B_IDXLO * 32 + j] = (int)(uint32_t)idx;
+                bi[B_IDXHI * 32 + j] = (int)(uint32_t)(idx >> 32);
+                bi[B_STATUS * 32 + j] = status;
+                bi[B_N1 * 32 + j] = L.n + 1;
+                bi[B_ONSET * 32 + j] = L.onset();
+            }
+            bcount += cnt;
+            need = endm;
+        }
+    }
 }
 
 ModelF32 to_f32(const ModelDev &m)
 {
     ModelF32 f;
-    f.g = (float)m.g;
-    f.rho = (float)m.rho;
-    f.area = (float)m.area;
-    f.hl = (float)m.hl;
-    f.beta = (float)m.beta;
-    f.phi_f = (float)m.phi_f;
     f.dt = (float)m.dt;
     f.h6 = (float)m.h6;
     f.nh2 = -(float)m.h2;
@@ -234,27 +462,29 @@ ModelF32 to_f32(const ModelDev &m)
     return f;
 }
 
-template <int CAP, bool LEAD, bool TTC>
+template <bool LEAD, bool TTC>
 cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, const WorkDev &w,
                      const LaunchCfg &cfg, cudaStream_t s)
 {
-    auto kern = k_rollout_fp32<CAP, LEAD, TTC>;
+    auto kern = k_rollout_fp32<LEAD, TTC>;
     int dev = 0, sms = 0, per_sm = cfg.blocks_per_sm;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     if (per_sm <= 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmemPerBlockAll);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    uint64_t tiles = (w.n + w.tile - 1) / w.tile;
+    const uint64_t tiles = (w.n + kTile - 1) / kTile;
     uint64_t blocks = (uint64_t)sms * per_sm;
-    uint64_t need_blocks = (tiles + 3) / 4;
+    const uint64_t need_blocks = (tiles + kWarps - 1) / kWarps;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, 128, 0, s>>>(m, to_f32(m), p, o, w);
+    WorkDev wt = w;
+    wt.tile = kTile;
+    kern<<<(unsigned)blocks, kThreads, kSmemPerBlockAll, s>>>(m, to_f32(m), p, o, wt);
     return cudaGetLastError();
 }
 
@@ -264,16 +494,9 @@ cudaError_t launch_rollout_fp32(const ModelDev &m, const ParamsDev &p, const Out
                                 const WorkDev &w, const LaunchCfg &cfg, cudaStream_t s)
 {
     const bool lead = m.lead != 0, ttc = m.trigger == AEB_TRIGGER_TTC;
-    if (m.cap_mode == AEB_CAP_LUMPED) {
-        if (lead) return ttc ? launch_t<AEB_CAP_LUMPED, true, true>(m, p, o, w, cfg, s)
-                             : launch_t<AEB_CAP_LUMPED, true, false>(m, p, o, w, cfg, s);
-        return ttc ? launch_t<AEB_CAP_LUMPED, false, true>(m, p, o, w, cfg, s)
-                   : launch_t<AEB_CAP_LUMPED, false, false>(m, p, o, w, cfg, s);
-    }
-    if (lead) return ttc ? launch_t<AEB_CAP_PER_AXLE, true, true>(m, p, o, w, cfg, s)
-                         : launch_t<AEB_CAP_PER_AXLE, true, false>(m, p, o, w, cfg, s);
-    return ttc ? launch_t<AEB_CAP_PER_AXLE, false, true>(m, p, o, w, cfg, s)
-               : launch_t<AEB_CAP_PER_AXLE, false, false>(m, p, o, w, cfg, s);
+    if (lead) return ttc ? launch_t<true, true>(m, p, o, w, cfg, s)
+                         : launch_t<true, false>(m, p, o, w, cfg, s);
+    return ttc ? launch_t<false, true>(m, p, o, w, cfg, s) : launch_t<false, false>(m, p, o, w, cfg, s);
 }
 
 }  // namespace aeb
