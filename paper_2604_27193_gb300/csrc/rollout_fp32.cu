@@ -68,7 +68,7 @@ enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 constexpr int kTileWords = (R_NF + R_NI) * kTile;
 
 struct ModelF32 {
-    float dt, h6, nh2, nh6, ndt, acmd, thr_h, thr_l;
+    float dt, h6, nh2, nh6, ndt, nc6, acmd, thr_h, thr_l;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -193,6 +193,107 @@ struct Lane32 {
     __device__ __forceinline__ void next_event(int32_t n_last)
     {
         ev = (trig && n_b >= n && n_b < n_last) ? n_b : n_last;
+    }
+
+    // Common tail of a step: position / speed increments, compensated updates,
+    // actuator decay.  Returns the end-of-step pairs in the out-parameters.
+    __device__ __forceinline__ void advance(const ModelF32 &F, float q1, float q2, float q3,
+                                            float q4, float &g1h, float &g1l, float &w1h,
+                                            float &w1l, float &en) const
+    {
+        // dv = -(dt/6)(q1 + 2 q2 + 2 q3 + q4); with v2 = vh - (dt/2) q1,
+        // v3 = vh - (dt/2) q2, v4 = vh - dt q3 the position increment
+        // (dt/6)(v + 2 v2 + 2 v3 + v4) is dt v - (dt^2/6)(q1 + q2 + q3)
+        const float s123 = (q1 + q2) + q3;
+        const float dv = F.nh6 * fmaf(2.0f, s123, q4 - q1);
+        const float dx = fmaf(F.dt, vl, fmaf(F.nc6, s123, F.dt * vh));
+        // Fast2Sum of (hi, lo + increment) keeps each pair normalised
+        const float tv = dv + vl;
+        w1h = vh + tv;
+        w1l = tv - (w1h - vh);
+        const float tg = gl - dx;
+        g1h = gh + tg;
+        g1l = tg - (g1h - gh);
+        en = fmaf(nmP, e, e);
+    }
+
+    __device__ __forceinline__ void commit(float g1h, float g1l, float w1h, float w1l, float en)
+    {
+        vh = w1h;
+        vl = w1l;
+        gh = g1h;
+        gl = g1l;
+        e = en;
+        n = n + 1;
+    }
+
+    // A step inside the current piece of r(D): one FMA per stage for r.
+    // Returns true if the rollout ended (contact or stop) in this step.
+    __device__ __forceinline__ bool step_fast(const ModelF32 &F, float &g1h, float &g1l,
+                                              float &w1h, float &w1l)
+    {
+        const float S = sp * e;
+        const float q1 = fmaf(k * vh, vh, fmaf(S, np1, C));
+        const float v2 = fmaf(F.nh2, q1, vh);
+        const float q2 = fmaf(k * v2, v2, fmaf(S, np2, C));
+        const float v3 = fmaf(F.nh2, q2, vh);
+        const float q3 = fmaf(k * v3, v3, fmaf(S, np3, C));
+        const float v4 = fmaf(F.ndt, q3, vh);
+        const float q4 = fmaf(k * v4, v4, fmaf(S, np4, C));
+        float en;
+        advance(F, q1, q2, q3, q4, g1h, g1l, w1h, w1l, en);
+        const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f;
+        if (!ended) commit(g1h, g1l, w1h, w1l, en);
+        return ended;
+    }
+
+    // Whether the next step may take the fast path.
+    __device__ __forceinline__ bool fast_next() const
+    {
+        return n != ev && !(e < eth) && (!TTC || trig);
+    }
+
+    // The brake-onset step, a step crossing a breakpoint of r(D), or the last
+    // step before the horizon: full minimum for r, then re-select the piece.
+    __device__ __forceinline__ bool step_slow(const ModelF32 &F, int32_t n_last, float &g1h,
+                                              float &g1l, float &w1h, float &w1l)
+    {
+        if (n == n_b) {  // the command switches on at the start of this step
+            u = F.acmd;
+            e = e - F.acmd;
+        }
+        const float q1 = fmaf(k * vh, vh, rg_full(np1));
+        const float v2 = fmaf(F.nh2, q1, vh);
+        const float q2 = fmaf(k * v2, v2, rg_full(np2));
+        const float v3 = fmaf(F.nh2, q2, vh);
+        const float q3 = fmaf(k * v3, v3, rg_full(np3));
+        const float v4 = fmaf(F.ndt, q3, vh);
+        const float q4 = fmaf(k * v4, v4, rg_full(np4));
+        float en;
+        advance(F, q1, q2, q3, q4, g1h, g1l, w1h, w1l, en);
+        const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
+        if (!ended) {
+            commit(g1h, g1l, w1h, w1l, en);
+            set_piece(-fmaf(-np1, e, u));
+            next_event(n_last);
+        }
+        return ended;
+    }
+
+    // TTC trigger (while not yet triggered): (g + noise) - thr v <= 0, with the
+    // exact rounding error of thr * vh; braking starts n_delay steps later.
+    __device__ __forceinline__ void ttc_check(const ModelF32 &F, int32_t n_last)
+    {
+        const float p = F.thr_h * vh;
+        const float pe = fmaf(F.thr_h, vh, -p);
+        const float hi = gh - p;
+        const float lo = (gl + nz) - (pe + fmaf(F.thr_h, vl, F.thr_l * vh));
+        if (hi + lo <= 0.0f) {
+            trig = true;
+            const long long nb = (long long)n + n_delay;
+            n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
+            ev = (n_b < n_last) ? n_b : n_last;
+        }
     }
 
     // Load sample `slot` of the warp's tile; true if it ended at once (stored).
@@ -348,85 +449,29 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
             }
         }
 
-        // ---- one RK4 step (Sec. IV-D) ----
-        int status = -1;
-        float g1h = 0.0f, g1l = 0.0f, w1h = 0.0f, w1l = 0.0f;
-        if (active) {
-            if (TTC && !L.trig) {
-                // (g + noise) - thr v <= 0, with the exact rounding error of thr * vh
-                const float p = F.thr_h * L.vh;
-                const float pe = fmaf(F.thr_h, L.vh, -p);
-                const float hi = L.gh - p;
-                const float lo = (L.gl + L.nz) - (pe + fmaf(F.thr_h, L.vl, F.thr_l * L.vh));
-                if (hi + lo <= 0.0f) {
-                    L.trig = true;
-                    const long long nb = (long long)L.n + L.n_delay;
-                    L.n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
-                    L.ev = (L.n_b < n_last) ? L.n_b : n_last;
-                }
-            }
-            const bool slow = (L.n == L.ev) || (L.e < L.eth);
-            float q1, q2, q3, q4, v2, v3, v4;
-            if (!slow) {
-                const float S = L.sp * L.e;
-                q1 = fmaf(L.k * L.vh, L.vh, fmaf(S, L.np1, L.C));
-                v2 = fmaf(F.nh2, q1, L.vh);
-                q2 = fmaf(L.k * v2, v2, fmaf(S, L.np2, L.C));
-                v3 = fmaf(F.nh2, q2, L.vh);
-                q3 = fmaf(L.k * v3, v3, fmaf(S, L.np3, L.C));
-                v4 = fmaf(F.ndt, q3, L.vh);
-                q4 = fmaf(L.k * v4, v4, fmaf(S, L.np4, L.C));
-            } else {
-                if (L.n == L.n_b) {  // brake onset at the start of this step
-                    L.u = F.acmd;
-                    L.e = L.e - F.acmd;
-                }
-                q1 = fmaf(L.k * L.vh, L.vh, L.rg_full(L.np1));
-                v2 = fmaf(F.nh2, q1, L.vh);
-                q2 = fmaf(L.k * v2, v2, L.rg_full(L.np2));
-                v3 = fmaf(F.nh2, q2, L.vh);
-                q3 = fmaf(L.k * v3, v3, L.rg_full(L.np3));
-                v4 = fmaf(F.ndt, q3, L.vh);
-                q4 = fmaf(L.k * v4, v4, L.rg_full(L.np4));
-            }
-            const float dv = F.nh6 * fmaf(2.0f, q2 + q3, q1 + q4);
-            const float dx = fmaf(F.dt, L.vl, F.h6 * fmaf(2.0f, v2 + v3, L.vh + v4));
-            // compensated updates: Fast2Sum of (hi, lo + increment) keeps each
-            // pair normalised (|lo| <= ulp(hi) / 2)
-            const float tv = dv + L.vl;
-            w1h = L.vh + tv;
-            w1l = tv - (w1h - L.vh);
-            const float tg = L.gl - dx;
-            g1h = L.gh + tg;
-            g1l = tg - (g1h - L.gh);
-            const float en = fmaf(L.nmP, L.e, L.e);
-            if (LEAD && g1h <= 0.0f)
-                status = AEB_CONTACT;
-            else if (w1h <= 0.0f)
-                status = AEB_STOP;
-            else if (slow && L.n >= n_last)
-                status = AEB_HORIZON;
-            if (status < 0) {
-                L.vh = w1h;
-                L.vl = w1l;
-                L.gh = g1h;
-                L.gl = g1l;
-                L.e = en;
-                L.n = L.n + 1;
-                if (slow) {
-                    L.set_piece(-fmaf(-L.np1, L.e, L.u));
-                    L.next_event(n_last);
-                }
-            }
+        // ---- up to two RK4 steps (Sec. IV-D) per lane ----
+        bool ended = false;
+        float g1h, g1l, w1h, w1l;
+        if (TTC && active && !L.trig) L.ttc_check(F, n_last);
+        const bool slow = active && ((L.n == L.ev) || (L.e < L.eth));
+        if (__any_sync(kFull, slow)) {  // warp-uniform: rare
+            if (slow) ended = L.step_slow(F, n_last, g1h, g1l, w1h, w1l);
         }
-        const unsigned endm = __ballot_sync(kFull, status >= 0);
+        if (active && !slow) {
+            ended = L.step_fast(F, g1h, g1l, w1h, w1l);
+            if (!ended && L.fast_next()) ended = L.step_fast(F, g1h, g1l, w1h, w1l);
+        }
+        const unsigned endm = __ballot_sync(kFull, ended);
         if (endm) {
             const int cnt = __popc(endm);
             if (bcount + cnt > 32) {
                 flush_batch(M, P, O, bf, bi, bcount);
                 bcount = 0;
             }
-            if (status >= 0) {
+            if (ended) {
+                const int status = (LEAD && g1h <= 0.0f)
+                                       ? AEB_CONTACT
+                                       : (w1h <= 0.0f ? AEB_STOP : AEB_HORIZON);
                 const int j = bcount + __popc(endm & lanemask_lt());
                 bf[B_G0H * 32 + j] = L.gh;
                 bf[B_G0L * 32 + j] = L.gl;
@@ -456,6 +501,7 @@ ModelF32 to_f32(const ModelDev &m)
     f.nh2 = -(float)m.h2;
     f.nh6 = -(float)m.h6;
     f.ndt = -(float)m.dt;
+    f.nc6 = (float)(-(m.dt * m.dt) / 6.0);
     f.acmd = (float)m.a_cmd;
     f.thr_h = (float)m.ttc_thr;
     f.thr_l = (float)(m.ttc_thr - (double)f.thr_h);
