@@ -54,6 +54,9 @@ namespace {
 constexpr int kTile = 64;      // samples per warp tile
 constexpr int kWarps = 4;      // warps per block
 constexpr int kThreads = 32 * kWarps;
+#ifndef AEB_FP32_WINDOW
+#define AEB_FP32_WINDOW 8      // steps a lane runs without termination tests
+#endif
 #ifndef AEB_FP32_MIN_BLOCKS
 #define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
 #endif
@@ -68,7 +71,7 @@ enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 constexpr int kTileWords = (R_NF + R_NI) * kTile;
 
 struct ModelF32 {
-    float dt, h6, nh2, nh6, ndt, nc6, acmd, thr_h, thr_l;
+    float dt, h6, nh2, nh6, ndt, acmd, thr_h, thr_l;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -142,7 +145,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 template <bool LEAD, bool TTC>
 struct Lane32 {
     float vh, vl, gh, gl, e;      // state: speed, gap d0 - x, actuator deviation a - u
-    float u, C, sp, eth;          // command, current piece of r(D)
+    float u, C, sp, eth, ethK;    // command, current piece of r(D), window threshold
     float k, gs, f0, f1, r0, r1, mg;
     float np1, np2, np3, np4, p4, nmP, nz;
     int32_t n, ev, n_b, n_delay;  // step, next slow step, onset step, delay steps
@@ -173,6 +176,15 @@ struct Lane32 {
         sp = bb;
         C = (ab - bb * u) + gs;
         eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
+        // e decays by (1 - mP) per step; a window of K steps stays inside the
+        // piece if its last step does: e (1 - mP)^(K-1) >= eth (with margin)
+        ethK = eth;
+        if (eth > 0.0f) {
+            float f = 1.0f;
+#pragma unroll
+            for (int j = 1; j < AEB_FP32_WINDOW; ++j) f *= (1.0f + nmP);
+            ethK = (f > 0.0f) ? (eth / f) * 1.000001f : finf();
+        }
     }
 
     // r + g sin(theta) by the full minimum (slow steps)
@@ -198,15 +210,15 @@ struct Lane32 {
     // Common tail of a step: position / speed increments, compensated updates,
     // actuator decay.  Returns the end-of-step pairs in the out-parameters.
     __device__ __forceinline__ void advance(const ModelF32 &F, float q1, float q2, float q3,
-                                            float q4, float &g1h, float &g1l, float &w1h,
-                                            float &w1l, float &en) const
+                                            float q4, float v2, float v3, float v4, float &g1h,
+                                            float &g1l, float &w1h, float &w1l, float &en) const
     {
-        // dv = -(dt/6)(q1 + 2 q2 + 2 q3 + q4); with v2 = vh - (dt/2) q1,
-        // v3 = vh - (dt/2) q2, v4 = vh - dt q3 the position increment
-        // (dt/6)(v + 2 v2 + 2 v3 + v4) is dt v - (dt^2/6)(q1 + q2 + q3)
-        const float s123 = (q1 + q2) + q3;
-        const float dv = F.nh6 * fmaf(2.0f, s123, q4 - q1);
-        const float dx = fmaf(F.dt, vl, fmaf(F.nc6, s123, F.dt * vh));
+        // Both increments carry the same binary32 step factor h6 = dt/6: a
+        // position increment formed with dt instead would scale distance
+        // against speed by the ratio of two independently rounded constants
+        // (a systematic ~5e-8 relative error in every stopping distance).
+        const float dv = F.nh6 * fmaf(2.0f, q2 + q3, q1 + q4);
+        const float dx = fmaf(F.dt, vl, F.h6 * fmaf(2.0f, v2 + v3, vh + v4));
         // Fast2Sum of (hi, lo + increment) keeps each pair normalised
         const float tv = dv + vl;
         w1h = vh + tv;
@@ -241,10 +253,60 @@ struct Lane32 {
         const float v4 = fmaf(F.ndt, q3, vh);
         const float q4 = fmaf(k * v4, v4, fmaf(S, np4, C));
         float en;
-        advance(F, q1, q2, q3, q4, g1h, g1l, w1h, w1l, en);
+        advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f;
         if (!ended) commit(g1h, g1l, w1h, w1l, en);
         return ended;
+    }
+
+    // Whether the next K steps may run as one window: no slow step among them
+    // and the trigger (if any) already fired.
+    __device__ __forceinline__ bool window_ok() const
+    {
+        return (!TTC || trig) && n + AEB_FP32_WINDOW <= ev && !(e < ethK);
+    }
+
+    // K fast steps with no termination test in between.  Within a few
+    // milliseconds a stop leaves v <= 0 and a contact leaves g <= 0 (a contact
+    // at near-zero speed turns into v <= 0), so the state after the window
+    // shows whether the rollout ended inside it; if so the window is undone and
+    // replayed one checked step at a time, which reproduces the same
+    // arithmetic and finds the terminating step.
+    __device__ __forceinline__ bool step_window(const ModelF32 &F, float &g1h, float &g1l,
+                                                float &w1h, float &w1l)
+    {
+        const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
+#pragma unroll
+        for (int j = 0; j < AEB_FP32_WINDOW; ++j) {
+            const float S = sp * e;
+            const float q1 = fmaf(k * vh, vh, fmaf(S, np1, C));
+            const float v2 = fmaf(F.nh2, q1, vh);
+            const float q2 = fmaf(k * v2, v2, fmaf(S, np2, C));
+            const float v3 = fmaf(F.nh2, q2, vh);
+            const float q3 = fmaf(k * v3, v3, fmaf(S, np3, C));
+            const float v4 = fmaf(F.ndt, q3, vh);
+            const float q4 = fmaf(k * v4, v4, fmaf(S, np4, C));
+            float en;
+            advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
+            vh = w1h;
+            vl = w1l;
+            gh = g1h;
+            gl = g1l;
+            e = en;
+        }
+        if ((LEAD && gh <= 0.0f) || vh <= 0.0f) {
+            vh = vh0;
+            vl = vl0;
+            gh = gh0;
+            gl = gl0;
+            e = e0;
+#pragma unroll 1
+            for (int j = 0; j < AEB_FP32_WINDOW; ++j)
+                if (step_fast(F, g1h, g1l, w1h, w1l)) return true;
+            return false;
+        }
+        n += AEB_FP32_WINDOW;
+        return false;
     }
 
     // Whether the next step may take the fast path.
@@ -270,7 +332,7 @@ struct Lane32 {
         const float v4 = fmaf(F.ndt, q3, vh);
         const float q4 = fmaf(k * v4, v4, rg_full(np4));
         float en;
-        advance(F, q1, q2, q3, q4, g1h, g1l, w1h, w1l, en);
+        advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
         if (!ended) {
             commit(g1h, g1l, w1h, w1l, en);
@@ -458,8 +520,12 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
             if (slow) ended = L.step_slow(F, n_last, g1h, g1l, w1h, w1l);
         }
         if (active && !slow) {
-            ended = L.step_fast(F, g1h, g1l, w1h, w1l);
-            if (!ended && L.fast_next()) ended = L.step_fast(F, g1h, g1l, w1h, w1l);
+            if (L.window_ok()) {
+                ended = L.step_window(F, g1h, g1l, w1h, w1l);
+            } else {
+                ended = L.step_fast(F, g1h, g1l, w1h, w1l);
+                if (!ended && L.fast_next()) ended = L.step_fast(F, g1h, g1l, w1h, w1l);
+            }
         }
         const unsigned endm = __ballot_sync(kFull, ended);
         if (endm) {
@@ -501,7 +567,6 @@ ModelF32 to_f32(const ModelDev &m)
     f.nh2 = -(float)m.h2;
     f.nh6 = -(float)m.h6;
     f.ndt = -(float)m.dt;
-    f.nc6 = (float)(-(m.dt * m.dt) / 6.0);
     f.acmd = (float)m.a_cmd;
     f.thr_h = (float)m.ttc_thr;
     f.thr_l = (float)(m.ttc_thr - (double)f.thr_h);
