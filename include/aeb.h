@@ -155,6 +155,34 @@ typedef struct aeb_stats {
     uint64_t hist_v[AEB_NBINS];
 } aeb_stats;
 
+/* One job of a batched launch (many scenarios with uneven
+ * sample counts in one persistent launch): its parameters are rows
+ * [param_offset, param_offset + n) of the device columns, its outputs rows
+ * [out_offset, out_offset + n) of the output columns; ttc_thr is its own TTC
+ * threshold (used when model.trigger is AEB_TRIGGER_TTC). */
+typedef struct aeb_job {
+    uint64_t param_offset;
+    uint64_t out_offset;
+    uint64_t n;
+    double ttc_thr;
+} aeb_job;
+
+/* Per-job reduction of a batched launch: aeb_stats without the histograms. */
+typedef struct aeb_job_stats {
+    uint64_t n, n_stop, n_contact, n_horizon, n_invalid, steps;
+    double sum_d, sumsq_d, min_d, max_d;  /* x_ref over stopped samples */
+    double sum_v, sumsq_v, min_v, max_v;  /* v_imp over contact samples */
+} aeb_job_stats;
+
+/* Launch shape of the rollout kernels (chosen by aeb_autotune or set). */
+typedef struct aeb_launch_config {
+    int32_t tile;           /* samples per warp tile: 32..256, multiple of 32   */
+    int32_t blocks_per_sm;  /* resident blocks per SM (0: as many as fit)       */
+} aeb_launch_config;
+
+/* Opaque batched-launch plan (device tables + captured CUDA graph). */
+typedef struct aeb_batch aeb_batch;
+
 /* ---- entry points -------------------------------------------------------- */
 
 /* ABI version of the loaded library (AEB_ABI_VERSION when it was built). */
@@ -249,6 +277,58 @@ aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n, const aeb_hist
 aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64_t n,
                         aeb_precision precision, const aeb_hist_spec *hist,
                         aeb_stats *host_stats, const aeb_outputs *host_out, void *stream);
+
+/*
+ * aeb_batch_create -- plan a batched launch over n_jobs jobs (
+ * the per-sample method is that of aeb_rollout, Sec. IV-D, V-A..V-D).  Builds
+ * the table of (job, tile) work items, allocates the device tables and
+ * scratch (owned by the plan), and captures one CUDA graph: reset of the work
+ * counter, one persistent rollout launch over all tiles, and the per-job
+ * fixed-order reduction into stats[0 .. n_jobs).
+ *   jobs       host array (copied)
+ *   params     device columns (caller-owned; must outlive the plan)
+ *   out        device output columns covering every job's out rows; status,
+ *              x_ref, v_imp and n_steps are required
+ *   stats      DEVICE array of n_jobs aeb_job_stats (caller-owned)
+ * The launch shape is the library's current configuration for `precision`.
+ * Synchronous (allocation, table upload, capture).  AEB_EINVAL on bad
+ * arguments (n_jobs == 0, NULL columns, a job with n > 2^32 - 1 tiles).
+ */
+aeb_status aeb_batch_create(const aeb_model *model, const aeb_job *jobs, uint32_t n_jobs,
+                            const aeb_params *params, aeb_precision precision,
+                            const aeb_outputs *out, aeb_job_stats *stats, aeb_batch **plan);
+
+/* aeb_batch_run -- launch the plan's graph on `stream` (asynchronous).  A plan
+ * may be run any number of times; runs of one plan must not overlap. */
+aeb_status aeb_batch_run(aeb_batch *plan, void *stream);
+
+/* aeb_batch_destroy -- wait for the plan's work and free it (NULL is a no-op). */
+void aeb_batch_destroy(aeb_batch *plan);
+
+/*
+ * aeb_rollout_batched -- create, run once on `stream` and destroy a plan
+ * (synchronous: returns when the stats are written).
+ */
+aeb_status aeb_rollout_batched(const aeb_model *model, const aeb_job *jobs, uint32_t n_jobs,
+                               const aeb_params *params, aeb_precision precision,
+                               const aeb_outputs *out, aeb_job_stats *stats, void *stream);
+
+/* Launch shape in use for `precision` (get / set).  Setting validates the
+ * shape (AEB_EINVAL) and applies to later launches and plans. */
+aeb_status aeb_get_launch_config(aeb_precision precision, aeb_launch_config *cfg);
+aeb_status aeb_set_launch_config(aeb_precision precision, const aeb_launch_config *cfg);
+
+/*
+ * aeb_autotune -- time the rollout of the first n samples of `params` under
+ * each candidate shape (tile 32/64/128 x blocks per SM 3..8 that fit), keep the
+ * fastest for `precision` and return it in *best.  If cache_path is not NULL,
+ * a shape recorded there for this device, precision and model mode is used
+ * without timing, and a newly timed one is recorded.  Synchronous; writes the
+ * outputs of the timed runs into `out`.
+ */
+aeb_status aeb_autotune(const aeb_model *model, const aeb_params *params, uint64_t n,
+                        aeb_precision precision, const aeb_outputs *out, void *stream,
+                        const char *cache_path, aeb_launch_config *best);
 
 #ifdef __cplusplus
 }

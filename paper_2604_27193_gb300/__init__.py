@@ -78,7 +78,24 @@ class Stats(C.Structure):
         [("hist_d", C.c_uint64 * NBINS), ("hist_v", C.c_uint64 * NBINS)]
 
 
+class Job(C.Structure):
+    _fields_ = [("param_offset", C.c_uint64), ("out_offset", C.c_uint64), ("n", C.c_uint64),
+                ("ttc_thr", C.c_double)]
+
+
+class JobStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n", "n_stop", "n_contact", "n_horizon", "n_invalid",
+                                          "steps")] + \
+        [(n, C.c_double) for n in ("sum_d", "sumsq_d", "min_d", "max_d", "sum_v", "sumsq_v",
+                                   "min_v", "max_v")]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
 STATS_BYTES = C.sizeof(Stats)
+JOB_STATS_BYTES = C.sizeof(JobStats)
 
 _lib = None
 _lock = threading.Lock()
@@ -108,7 +125,20 @@ def lib():
                                      C.c_void_p]
             L.aeb_evaluate.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32,
                                        P(HistSpec), P(Stats), P(Outputs), C.c_void_p]
-            for fn in ("aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate"):
+            L.aeb_batch_create.argtypes = [P(Model), P(Job), C.c_uint32, P(Params), C.c_int32,
+                                           P(Outputs), C.c_void_p, P(C.c_void_p)]
+            L.aeb_batch_run.argtypes = [C.c_void_p, C.c_void_p]
+            L.aeb_batch_destroy.argtypes = [C.c_void_p]
+            L.aeb_batch_destroy.restype = None
+            L.aeb_rollout_batched.argtypes = [P(Model), P(Job), C.c_uint32, P(Params), C.c_int32,
+                                              P(Outputs), C.c_void_p, C.c_void_p]
+            L.aeb_get_launch_config.argtypes = [C.c_int32, P(LaunchConfig)]
+            L.aeb_set_launch_config.argtypes = [C.c_int32, P(LaunchConfig)]
+            L.aeb_autotune.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32, P(Outputs),
+                                       C.c_void_p, C.c_char_p, P(LaunchConfig)]
+            for fn in ("aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate",
+                       "aeb_batch_create", "aeb_batch_run", "aeb_rollout_batched",
+                       "aeb_get_launch_config", "aeb_set_launch_config", "aeb_autotune"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != 1:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -236,6 +266,73 @@ def aeb_evaluate(m, params_host: dict, n: int, precision: int, hist: HistSpec,
                               C.byref(st), C.byref(os_) if os_ is not None else None,
                               _stream(stream)))
     return st
+
+
+def jobs_array(jobs) -> "C.Array":
+    """ctypes array of aeb_job from (param_offset, out_offset, n, ttc_thr) tuples."""
+    arr = (Job * len(jobs))()
+    for k, (po, oo, n, thr) in enumerate(jobs):
+        arr[k] = Job(po, oo, n, thr)
+    return arr
+
+
+class BatchPlan:
+    """aeb_batch_create / aeb_batch_run / aeb_batch_destroy."""
+
+    def __init__(self, m, jobs, params: dict, precision: int, out: dict, stats_dev):
+        self._jobs = jobs_array(jobs)
+        ms, ps, os_ = model(m), params_struct(params), outputs_struct(out)
+        self._h = C.c_void_p()
+        _check(lib().aeb_batch_create(C.byref(ms), self._jobs, len(jobs), C.byref(ps), precision,
+                                      C.byref(os_), _ptr(stats_dev), C.byref(self._h)))
+
+    def run(self, stream=None):
+        _check(lib().aeb_batch_run(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().aeb_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def aeb_rollout_batched(m, jobs, params: dict, precision: int, out: dict, stats_dev,
+                        stream=None):
+    arr = jobs_array(jobs)
+    ms, ps, os_ = model(m), params_struct(params), outputs_struct(out)
+    _check(lib().aeb_rollout_batched(C.byref(ms), arr, len(jobs), C.byref(ps), precision,
+                                     C.byref(os_), _ptr(stats_dev), _stream(stream)))
+
+
+def aeb_get_launch_config(precision: int) -> LaunchConfig:
+    c = LaunchConfig()
+    _check(lib().aeb_get_launch_config(precision, C.byref(c)))
+    return c
+
+
+def aeb_set_launch_config(precision: int, tile: int, blocks_per_sm: int):
+    c = LaunchConfig(tile, blocks_per_sm)
+    _check(lib().aeb_set_launch_config(precision, C.byref(c)))
+
+
+def aeb_autotune(m, params: dict, n: int, precision: int, out: dict, stream=None,
+                 cache_path: str | None = None) -> LaunchConfig:
+    c = LaunchConfig()
+    ms, ps, os_ = model(m), params_struct(params), outputs_struct(out)
+    _check(lib().aeb_autotune(C.byref(ms), C.byref(ps), n, precision, C.byref(os_),
+                              _stream(stream), cache_path.encode() if cache_path else None,
+                              C.byref(c)))
+    return c
+
+
+def job_stats_from_buffer(buf, n_jobs: int):
+    raw = buf.cpu().numpy().tobytes() if hasattr(buf, "cpu") else bytes(buf)
+    return (JobStats * n_jobs).from_buffer_copy(raw[:JOB_STATS_BYTES * n_jobs])
 
 
 # --------------------------------------------------------------------------

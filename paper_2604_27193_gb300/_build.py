@@ -27,7 +27,7 @@ CU_SOURCES = {
     "reduce.cu": [],
     "reduce_noalloc.cu": [],
 }
-CPP_SOURCES = ["capi.cpp", "sampler.cpp"]
+CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp"]
 HEADERS = ["aeb_internal.h", "rollout_common.cuh", "host_util.h"]
 
 

@@ -30,12 +30,31 @@ struct OutDev {
     int32_t *n_steps, *n_onset;
 };
 
-// Work split: samples [0, n) in tiles of `tile` consecutive samples, handed
-// to warps through one 64-bit counter that must be zero at launch.
+// A job: `n` samples whose parameters start at row `param_offset` of the
+// columns and whose outputs start at row `out_offset`; `ttc_thr` is its TTC
+// threshold (TTC trigger mode).
+struct JobDev {
+    uint64_t param_offset, out_offset, n;
+    double ttc_thr;
+};
+
+// A tile: `count` consecutive samples of job `job`, from its sample `first`.
+struct TileDesc {
+    uint64_t first;
+    uint32_t job, count;
+};
+
+// Work split, handed to warps through one 64-bit counter that must be zero at
+// launch.  Flat mode (tiles == nullptr): samples [0, n) of one job in tiles of
+// `tile` samples, parameters and outputs at the same row, the model's TTC
+// threshold.  Table mode: tile t is tiles[t] of job jobs[tiles[t].job].
 struct WorkDev {
     uint64_t n;
     uint32_t tile;
     unsigned long long *counter;
+    const TileDesc *tiles;
+    uint64_t n_tiles;
+    const JobDev *jobs;
 };
 
 struct LaunchCfg {
@@ -60,7 +79,21 @@ cudaError_t launch_reduce(const uint8_t *status, const double *x_ref, const doub
                           const int32_t *n_steps, uint64_t n, const aeb_hist_spec &h,
                           RedPartial *partials, aeb_stats *stats, cudaStream_t stream);
 
+// Per-job reduction: partials over the segments `blocks` (8192 rows at most,
+// each inside one job), then job j adds partials [first[j], first[j+1]).
+constexpr uint32_t kRedSegment = 8192;
+cudaError_t launch_reduce_jobs(const uint8_t *status, const double *x_ref, const double *v_imp,
+                               const int32_t *n_steps, const TileDesc *blocks, uint32_t n_blocks,
+                               const uint32_t *first, const JobDev *jobs, uint32_t n_jobs,
+                               RedPartial *partials, aeb_job_stats *stats, cudaStream_t s);
+
 // Host-side helpers shared by the C-ABI glue.
 int64_t steps_to_reach_host(double t, double dt);
+LaunchCfg launch_cfg(aeb_precision precision);
+void set_launch_cfg(aeb_precision precision, const LaunchCfg &cfg);
+aeb_status check_model(const aeb_model *m, ModelDev *out);
+aeb_status check_params(const aeb_params *p, ParamsDev *out);
+OutDev out_dev(const aeb_outputs *o);
+aeb_status cuda_fail(cudaError_t e, const char *what);
 
 }  // namespace aeb

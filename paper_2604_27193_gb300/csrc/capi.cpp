@@ -25,8 +25,6 @@ aeb_status fail(aeb_status code, const std::string &msg)
     return code;
 }
 
-namespace {
-
 aeb_status cuda_fail(cudaError_t e, const char *what)
 {
     const aeb_status code = (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
@@ -38,12 +36,16 @@ aeb_status cuda_fail(cudaError_t e, const char *what)
                           cudaGetErrorString(e) + ")");
 }
 
+namespace {
+
 bool is_pow2(double w)
 {
     if (!(w > 0.0) || !std::isfinite(w)) return false;
     int ex = 0;
     return std::frexp(w, &ex) == 0.5;
 }
+
+}  // namespace
 
 aeb_status check_model(const aeb_model *m, ModelDev *out)
 {
@@ -95,6 +97,8 @@ aeb_status check_params(const aeb_params *p, ParamsDev *out)
     return AEB_OK;
 }
 
+namespace {
+
 aeb_status check_hist(const aeb_hist_spec *h)
 {
     if (!h) return fail(AEB_EINVAL, "hist spec is NULL");
@@ -104,6 +108,8 @@ aeb_status check_hist(const aeb_hist_spec *h)
         return fail(AEB_EINVAL, "hist width must be a positive power of two");
     return AEB_OK;
 }
+
+}  // namespace
 
 OutDev out_dev(const aeb_outputs *o)
 {
@@ -119,6 +125,8 @@ OutDev out_dev(const aeb_outputs *o)
     }
     return d;
 }
+
+namespace {
 
 // Library scratch, one region per (device, stream): work on one stream is
 // ordered, so consecutive calls on a stream may reuse its region, while calls
@@ -156,7 +164,8 @@ aeb_status scratch_for(cudaStream_t s, size_t bytes, void **out)
     return AEB_OK;
 }
 
-LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 256}};
+std::mutex g_cfg_mu;
+LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 64}};
 
 aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
                         aeb_precision precision, const OutDev &od, cudaStream_t s)
@@ -167,8 +176,8 @@ aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
     auto *counter = static_cast<unsigned long long *>(scratch);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
-    const LaunchCfg &cfg = g_cfg[precision];
-    WorkDev w{n, (uint32_t)cfg.tile, counter};
+    const LaunchCfg cfg = launch_cfg(precision);
+    WorkDev w{n, (uint32_t)cfg.tile, counter, nullptr, 0, nullptr};
     e = (precision == AEB_FP64_PLAIN) ? launch_rollout_fp64(md, pd, od, w, cfg, s)
                                       : launch_rollout_fp32(md, pd, od, w, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -200,6 +209,18 @@ constexpr size_t kEvalBytesPerSample = 8 * AEB_NFIELDS + 1 + 8 * 4 + 4 * 2;
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
+
+LaunchCfg launch_cfg(aeb_precision precision)
+{
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    return g_cfg[precision == AEB_FP64_PLAIN ? 0 : 1];
+}
+
+void set_launch_cfg(aeb_precision precision, const LaunchCfg &cfg)
+{
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_cfg[precision == AEB_FP64_PLAIN ? 0 : 1] = cfg;
+}
 
 int64_t steps_to_reach_host(double t, double dt)
 {

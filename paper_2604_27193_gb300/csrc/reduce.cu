@@ -100,24 +100,38 @@ __device__ __forceinline__ RedPartial block_combine(RedPartial acc, RedPartial *
     return acc;
 }
 
+// HIST: accumulate the two histograms.  With a block table, block b reduces
+// rows [out_offset + first, + count) of job table[b].job (a segment of one
+// job), otherwise rows [b chunk, (b+1) chunk) of [0, n).
+template <bool HIST>
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
                  const double *__restrict__ vi, const int32_t *__restrict__ ns, uint64_t n,
-                 uint64_t chunk, double lo_d, double inv_wd, double lo_v, double inv_wv,
+                 uint64_t chunk, const TileDesc *__restrict__ table, const JobDev *__restrict__ jobs,
+                 double lo_d, double inv_wd, double lo_v, double inv_wv,
                  RedPartial *__restrict__ part, unsigned long long *__restrict__ hist_d,
                  unsigned long long *__restrict__ hist_v)
 {
-    __shared__ unsigned int sh_d[AEB_NBINS];
-    __shared__ unsigned int sh_v[AEB_NBINS];
+    __shared__ unsigned int sh_d[HIST ? AEB_NBINS : 1];
+    __shared__ unsigned int sh_v[HIST ? AEB_NBINS : 1];
     __shared__ RedPartial sh_p[kRedWarps];
-    for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
-        sh_d[j] = 0u;
-        sh_v[j] = 0u;
+    if (HIST) {
+        for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
+            sh_d[j] = 0u;
+            sh_v[j] = 0u;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    const uint64_t lo = (uint64_t)blockIdx.x * chunk;
-    const uint64_t hi = (lo + chunk < n) ? lo + chunk : n;
+    uint64_t lo, hi;
+    if (table) {
+        const TileDesc d = table[blockIdx.x];
+        lo = jobs[d.job].out_offset + d.first;
+        hi = lo + d.count;
+    } else {
+        lo = (uint64_t)blockIdx.x * chunk;
+        hi = (lo + chunk < n) ? lo + chunk : n;
+    }
     RedPartial acc;
     init_partial(acc);
     for (uint64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
@@ -130,7 +144,7 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
             acc.sumsq_d += d * d;
             acc.min_d = fmin(acc.min_d, d);
             acc.max_d = fmax(acc.max_d, d);
-            atomicAdd(&sh_d[bin_index(d, lo_d, inv_wd)], 1u);
+            if (HIST) atomicAdd(&sh_d[bin_index(d, lo_d, inv_wd)], 1u);
         } else if (s == AEB_CONTACT) {
             const double v = vi[i];
             acc.n_contact++;
@@ -138,7 +152,7 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
             acc.sumsq_v += v * v;
             acc.min_v = fmin(acc.min_v, v);
             acc.max_v = fmax(acc.max_v, v);
-            atomicAdd(&sh_v[bin_index(v, lo_v, inv_wv)], 1u);
+            if (HIST) atomicAdd(&sh_v[bin_index(v, lo_v, inv_wv)], 1u);
         } else if (s == AEB_HORIZON) {
             acc.n_horizon++;
         } else {
@@ -147,10 +161,42 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
     }
     acc = block_combine(acc, sh_p);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
-    __syncthreads();
-    for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
-        if (sh_d[j]) atomicAdd(&hist_d[j], (unsigned long long)sh_d[j]);
-        if (sh_v[j]) atomicAdd(&hist_v[j], (unsigned long long)sh_v[j]);
+    if (HIST) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < AEB_NBINS; j += kRedThreads) {
+            if (sh_d[j]) atomicAdd(&hist_d[j], (unsigned long long)sh_d[j]);
+            if (sh_v[j]) atomicAdd(&hist_v[j], (unsigned long long)sh_v[j]);
+        }
+    }
+}
+
+// Block j adds the partials [first[j], first[j+1]) of job j in index order.
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce_jobs_final(const RedPartial *__restrict__ part, const uint32_t *__restrict__ first,
+                    const JobDev *__restrict__ jobs, aeb_job_stats *__restrict__ out)
+{
+    __shared__ RedPartial sh_p[kRedWarps];
+    const uint32_t b0 = first[blockIdx.x], b1 = first[blockIdx.x + 1];
+    RedPartial acc;
+    init_partial(acc);
+    for (uint32_t j = b0 + threadIdx.x; j < b1; j += kRedThreads) add_partial(acc, part[j]);
+    acc = block_combine(acc, sh_p);
+    if (threadIdx.x == 0) {
+        aeb_job_stats &o = out[blockIdx.x];
+        o.n = jobs[blockIdx.x].n;
+        o.n_stop = acc.n_stop;
+        o.n_contact = acc.n_contact;
+        o.n_horizon = acc.n_horizon;
+        o.n_invalid = acc.n_invalid;
+        o.steps = acc.steps;
+        o.sum_d = acc.sum_d;
+        o.sumsq_d = acc.sumsq_d;
+        o.min_d = acc.min_d;
+        o.max_d = acc.max_d;
+        o.sum_v = acc.sum_v;
+        o.sumsq_v = acc.sumsq_v;
+        o.min_v = acc.min_v;
+        o.max_v = acc.max_v;
     }
 }
 
@@ -203,13 +249,29 @@ cudaError_t launch_reduce(const uint8_t *status, const double *x_ref, const doub
     const uint64_t chunk = (n + (uint64_t)g - 1) / (uint64_t)g;
     cudaError_t e = cudaMemsetAsync(stats->hist_d, 0, 2 * sizeof(uint64_t) * AEB_NBINS, s);
     if (e != cudaSuccess) return e;
-    k_reduce_partial<<<g, kRedThreads, 0, s>>>(
-        status, x_ref, v_imp, n_steps, n, chunk, h.lo_d, 1.0 / h.w_d, h.lo_v, 1.0 / h.w_v,
-        partials, reinterpret_cast<unsigned long long *>(stats->hist_d),
+    k_reduce_partial<true><<<g, kRedThreads, 0, s>>>(
+        status, x_ref, v_imp, n_steps, n, chunk, nullptr, nullptr, h.lo_d, 1.0 / h.w_d, h.lo_v,
+        1.0 / h.w_v, partials, reinterpret_cast<unsigned long long *>(stats->hist_d),
         reinterpret_cast<unsigned long long *>(stats->hist_v));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_final<<<1, kRedThreads, 0, s>>>(partials, g, n, h, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_jobs(const uint8_t *status, const double *x_ref, const double *v_imp,
+                               const int32_t *n_steps, const TileDesc *blocks, uint32_t n_blocks,
+                               const uint32_t *first, const JobDev *jobs, uint32_t n_jobs,
+                               RedPartial *partials, aeb_job_stats *stats, cudaStream_t s)
+{
+    if (n_blocks > 0) {
+        k_reduce_partial<false><<<n_blocks, kRedThreads, 0, s>>>(
+            status, x_ref, v_imp, n_steps, 0, 0, blocks, jobs, 0.0, 1.0, 0.0, 1.0, partials,
+            nullptr, nullptr);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_reduce_jobs_final<<<n_jobs, kRedThreads, 0, s>>>(partials, first, jobs, stats);
     return cudaGetLastError();
 }
 

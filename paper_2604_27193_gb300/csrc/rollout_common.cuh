@@ -17,37 +17,87 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
+// A claimed tile: `count` samples with parameters at rows p0.. and outputs at
+// rows o0.., and the TTC threshold of their job.  Warp-uniform.
+struct Tile {
+    uint64_t p0, o0;
+    int count;
+    double thr;
+    bool ok;
+};
+
+// Claim the next tile (all 32 lanes call together; lane 0 takes the ticket).
+__device__ __forceinline__ Tile claim_tile(const WorkDev &w, uint32_t tile_size, double model_thr)
+{
+    unsigned long long t = 0;
+    if ((threadIdx.x & 31u) == 0) t = atomicAdd(w.counter, 1ull);
+    t = __shfl_sync(kFull, t, 0);
+    Tile r;
+    if (!w.tiles) {
+        const uint64_t start = (uint64_t)t * tile_size;
+        r.ok = start < w.n;
+        r.p0 = r.o0 = start;
+        r.count = r.ok ? (int)((w.n - start < (uint64_t)tile_size) ? w.n - start : tile_size) : 0;
+        r.thr = model_thr;
+    } else {
+        r.ok = t < w.n_tiles;
+        r.count = 0;
+        r.p0 = r.o0 = 0;
+        r.thr = model_thr;
+        if (r.ok) {
+            const TileDesc d = w.tiles[t];
+            const JobDev j = w.jobs[d.job];
+            r.p0 = j.param_offset + d.first;
+            r.o0 = j.out_offset + d.first;
+            r.count = (int)d.count;
+            r.thr = j.ttc_thr;
+        }
+    }
+    return r;
+}
+
+// Number of tiles a launch walks.
+__host__ __forceinline__ uint64_t tiles_of(const WorkDev &w, uint32_t tile_size)
+{
+    return w.tiles ? w.n_tiles : (w.n + tile_size - 1) / tile_size;
+}
+
 // A warp's cursor into the sample tiles.  All 32 lanes call take() together
 // with the same `need` mask (the lanes whose rollout just ended).  Each lane
-// in `need` receives the next unclaimed sample index of the warp's tile; when
-// the tile is used up the warp claims the next tile from the global counter.
-// Lanes get kNone once every tile has been claimed.  Sample order inside a
-// warp depends only on when its lanes finish, never on other warps, but which
-// tiles a warp owns depends on timing: per-sample results never do.
+// in `need` receives the next unclaimed sample of the warp's tile (its
+// parameter row, output row and TTC threshold); when the tile is used up the
+// warp claims the next tile.  Lanes get false once every tile has been
+// claimed.  Per-sample results never depend on which warp runs a sample.
 struct WarpQueue {
-    uint64_t cur = 0, end = 0;  // warp-uniform
+    Tile cur{};
+    int used = 0;
     bool dry = false;
 
-    __device__ __forceinline__ uint64_t take(unsigned need, const WorkDev &w)
+    __device__ __forceinline__ bool take(unsigned need, const WorkDev &w, uint32_t tile_size,
+                                         double model_thr, uint64_t &pidx, uint64_t &oidx,
+                                         double &thr)
     {
         const unsigned lane = threadIdx.x & 31u;
-        uint64_t mine = kNone;
+        bool mine = false;
         while (need && !dry) {
-            if (cur >= end) {
-                unsigned long long t = 0;
-                if (lane == 0) t = atomicAdd(w.counter, 1ull);
-                t = __shfl_sync(kFull, t, 0);
-                uint64_t start = (uint64_t)t * w.tile;
-                if (start >= w.n) { dry = true; break; }
-                cur = start;
-                end = (start + w.tile < w.n) ? start + w.tile : w.n;
+            if (used >= cur.count) {
+                cur = claim_tile(w, tile_size, model_thr);
+                used = 0;
+                if (!cur.ok) {
+                    dry = true;
+                    break;
+                }
             }
-            uint64_t avail = end - cur;
-            unsigned rank = __popc(need & lanemask_lt());
-            bool got = ((need >> lane) & 1u) && rank < avail;
-            if (got) mine = cur + rank;
-            unsigned taken = __ballot_sync(kFull, got);
-            cur += __popc(taken);
+            const unsigned rank = __popc(need & lanemask_lt());
+            const bool got = ((need >> lane) & 1u) && (int)rank < cur.count - used;
+            if (got) {
+                mine = true;
+                pidx = cur.p0 + used + rank;
+                oidx = cur.o0 + used + rank;
+                thr = cur.thr;
+            }
+            const unsigned taken = __ballot_sync(kFull, got);
+            used += __popc(taken);
             need &= ~taken;
         }
         return mine;
@@ -114,30 +164,28 @@ namespace aeb {
 // loop ends when no lane holds a rollout.
 template <class Lane, class X>
 __device__ __forceinline__ void rollout_driver(const ModelDev &M, const X &Xc, const ParamsDev &P,
-                                               const OutDev &O, const WorkDev &W)
+                                               const OutDev &O, const WorkDev &W, uint32_t tile_size)
 {
     const unsigned lane = threadIdx.x & 31u;
     WarpQueue q;
     Lane L;
-    uint64_t idx = 0;
+    uint64_t pidx = 0, oidx = 0;
+    double thr = M.ttc_thr;
     bool active = false;
     unsigned need = kFull;
     for (;;) {
         while (need) {
-            uint64_t got = q.take(need, W);
+            const bool got = q.take(need, W, tile_size, M.ttc_thr, pidx, oidx, thr);
             bool ended = false;
             if ((need >> lane) & 1u) {
-                active = (got != kNone);
-                if (active) {
-                    idx = got;
-                    ended = L.init(M, Xc, P, O, idx);
-                }
+                active = got;
+                if (active) ended = L.init(M, Xc, P, O, pidx, oidx, thr);
             }
             need = __ballot_sync(kFull, ended);
         }
         if (!__any_sync(kFull, active)) return;
         bool ended = false;
-        if (active) ended = L.step(M, Xc, P, O, idx);
+        if (active) ended = L.step(M, Xc, P, O, oidx);
         need = __ballot_sync(kFull, ended);
     }
 }

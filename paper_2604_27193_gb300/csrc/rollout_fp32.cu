@@ -51,7 +51,8 @@
 namespace aeb {
 namespace {
 
-constexpr int kTile = 64;      // samples per warp tile
+constexpr int kTileDefault = 64;  // samples per warp tile unless configured
+constexpr int kTileMax = 256;
 constexpr int kWarps = 4;      // warps per block
 constexpr int kThreads = 32 * kWarps;
 #ifndef AEB_FP32_WINDOW
@@ -68,10 +69,9 @@ enum {
 };
 enum { R_NDELAY, R_KIND, R_NI };  // int fields
 enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
-constexpr int kTileWords = (R_NF + R_NI) * kTile;
 
 struct ModelF32 {
-    float dt, h6, nh2, nh6, ndt, acmd, thr_h, thr_l;
+    float dt, h6, nh2, nh6, ndt, acmd;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -79,7 +79,7 @@ __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 // Prepare samples [start, start + cnt) of a tile into the warp's shared slab.
 template <bool LEAD, bool TTC>
 __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P, uint64_t start,
-                                          int cnt, float *tf, int *ti)
+                                          int cnt, int T, float *tf, int *ti)
 {
     for (int j = threadIdx.x & 31; j < cnt; j += 32) {
         const uint64_t i = start + j;
@@ -94,51 +94,51 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
             else if (f[kV0] <= 0.0) kind = K_STOP0;
             else if (M.n_max == 0) kind = K_HORIZON0;
         }
-        ti[R_NDELAY * kTile + j] = nd;
-        ti[R_KIND * kTile + j] = kind;
+        ti[R_NDELAY * T + j] = nd;
+        ti[R_KIND * T + j] = kind;
         if (kind != K_RUN) continue;
         const float v0h = __double2float_rn(f[kV0]);
         const float d0h = __double2float_rn(f[kD0]);
-        tf[R_V0H * kTile + j] = v0h;
-        tf[R_V0L * kTile + j] = __double2float_rn(f[kV0] - (double)v0h);
-        tf[R_D0H * kTile + j] = d0h;
-        tf[R_D0L * kTile + j] = __double2float_rn(f[kD0] - (double)d0h);
-        tf[R_GS * kTile + j] = __double2float_rn(f[kGs]);
-        tf[R_K * kTile + j] = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
+        tf[R_V0H * T + j] = v0h;
+        tf[R_V0L * T + j] = __double2float_rn(f[kV0] - (double)v0h);
+        tf[R_D0H * T + j] = d0h;
+        tf[R_D0L * T + j] = __double2float_rn(f[kD0] - (double)d0h);
+        tf[R_GS * T + j] = __double2float_rn(f[kGs]);
+        tf[R_K * T + j] = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
         const double mu = f[kMu], mh = mu * M.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
-            tf[R_F0 * kTile + j] = finf();
-            tf[R_F1 * kTile + j] = 0.0f;
-            tf[R_R0 * kTile + j] = finf();
-            tf[R_R1 * kTile + j] = 0.0f;
-            tf[R_MG * kTile + j] = __double2float_rn((mu * M.g) / (1.0 + mh));
+            tf[R_F0 * T + j] = finf();
+            tf[R_F1 * T + j] = 0.0f;
+            tf[R_R0 * T + j] = finf();
+            tf[R_R1 * T + j] = 0.0f;
+            tf[R_MG * T + j] = __double2float_rn((mu * M.g) / (1.0 + mh));
         } else {
             const double mg = mu * f[kGc], im = 1.0 / (1.0 - mh), ip = 1.0 / (1.0 + mh);
-            tf[R_F0 * kTile + j] = __double2float_rn((mg * M.phi_f) * im);
-            tf[R_F1 * kTile + j] = __double2float_rn((1.0 - M.beta) * im);
-            tf[R_R0 * kTile + j] = __double2float_rn((mg * (1.0 - M.phi_f)) * ip);
-            tf[R_R1 * kTile + j] = __double2float_rn(M.beta * ip);
-            tf[R_MG * kTile + j] = __double2float_rn(mg);
+            tf[R_F0 * T + j] = __double2float_rn((mg * M.phi_f) * im);
+            tf[R_F1 * T + j] = __double2float_rn((1.0 - M.beta) * im);
+            tf[R_R0 * T + j] = __double2float_rn((mg * (1.0 - M.phi_f)) * ip);
+            tf[R_R1 * T + j] = __double2float_rn(M.beta * ip);
+            tf[R_MG * T + j] = __double2float_rn(mg);
         }
         if (f[kTau] > 0.0) {
             const double z = M.dt / f[kTau];
             const double p4 = 1.0 - z + 0.5 * z * z - 0.25 * z * z * z;
-            tf[R_NP1 * kTile + j] = -1.0f;
-            tf[R_NP2 * kTile + j] = __double2float_rn(-(1.0 - 0.5 * z));
-            tf[R_NP3 * kTile + j] = __double2float_rn(-(1.0 - 0.5 * z + 0.25 * z * z));
-            tf[R_NP4 * kTile + j] = __double2float_rn(-p4);
-            tf[R_P4 * kTile + j] = __double2float_rn(p4);
-            tf[R_NMP * kTile + j] =
+            tf[R_NP1 * T + j] = -1.0f;
+            tf[R_NP2 * T + j] = __double2float_rn(-(1.0 - 0.5 * z));
+            tf[R_NP3 * T + j] = __double2float_rn(-(1.0 - 0.5 * z + 0.25 * z * z));
+            tf[R_NP4 * T + j] = __double2float_rn(-p4);
+            tf[R_P4 * T + j] = __double2float_rn(p4);
+            tf[R_NMP * T + j] =
                 __double2float_rn(-(z * (1.0 + z * (-0.5 + z * (1.0 / 6.0 - z / 24.0)))));
         } else {
-            tf[R_NP1 * kTile + j] = 0.0f;
-            tf[R_NP2 * kTile + j] = 0.0f;
-            tf[R_NP3 * kTile + j] = 0.0f;
-            tf[R_NP4 * kTile + j] = 0.0f;
-            tf[R_P4 * kTile + j] = 0.0f;
-            tf[R_NMP * kTile + j] = -1.0f;
+            tf[R_NP1 * T + j] = 0.0f;
+            tf[R_NP2 * T + j] = 0.0f;
+            tf[R_NP3 * T + j] = 0.0f;
+            tf[R_NP4 * T + j] = 0.0f;
+            tf[R_P4 * T + j] = 0.0f;
+            tf[R_NMP * T + j] = -1.0f;
         }
-        tf[R_NZ * kTile + j] = TTC ? __double2float_rn(f[kNoise]) : 0.0f;
+        tf[R_NZ * T + j] = TTC ? __double2float_rn(f[kNoise]) : 0.0f;
     }
 }
 
@@ -147,7 +147,7 @@ struct Lane32 {
     float vh, vl, gh, gl, e;      // state: speed, gap d0 - x, actuator deviation a - u
     float u, C, sp, eth, ethK;    // command, current piece of r(D), window threshold
     float k, gs, f0, f1, r0, r1, mg;
-    float np1, np2, np3, np4, p4, nmP, nz;
+    float np1, np2, np3, np4, p4, nmP, nz, thr_h, thr_l;
     int32_t n, ev, n_b, n_delay;  // step, next slow step, onset step, delay steps
     bool trig;
 
@@ -346,10 +346,10 @@ struct Lane32 {
     // exact rounding error of thr * vh; braking starts n_delay steps later.
     __device__ __forceinline__ void ttc_check(const ModelF32 &F, int32_t n_last)
     {
-        const float p = F.thr_h * vh;
-        const float pe = fmaf(F.thr_h, vh, -p);
+        const float p = thr_h * vh;
+        const float pe = fmaf(thr_h, vh, -p);
         const float hi = gh - p;
-        const float lo = (gl + nz) - (pe + fmaf(F.thr_h, vl, F.thr_l * vh));
+        const float lo = (gl + nz) - (pe + fmaf(thr_h, vl, thr_l * vh));
         if (hi + lo <= 0.0f) {
             trig = true;
             const long long nb = (long long)n + n_delay;
@@ -358,19 +358,21 @@ struct Lane32 {
         }
     }
 
-    // Load sample `slot` of the warp's tile; true if it ended at once (stored).
+    // Load sample `slot` of the warp's tile (parameter row pi, output row i, TTC
+    // threshold thr); true if it ended at once (stored).
     __device__ __forceinline__ bool init(const ModelDev &M, const ParamsDev &P, const OutDev &O,
-                                         uint64_t i, int slot, const float *tf, const int *ti)
+                                         uint64_t pi, uint64_t i, double thr, int slot, int T,
+                                         const float *tf, const int *ti)
     {
-        const int kind = ti[R_KIND * kTile + slot];
-        n_delay = ti[R_NDELAY * kTile + slot];
+        const int kind = ti[R_KIND * T + slot];
+        n_delay = ti[R_NDELAY * T + slot];
         if (kind != K_RUN) {
             const int32_t on = TTC ? -1 : n_delay;
             if (kind == K_INVALID) {
                 const double nan = __longlong_as_double(0x7ff8000000000000ll);
                 store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
             } else if (kind == K_CONTACT0) {
-                store_out(O, i, AEB_CONTACT, 0.0, 0.0, __ldg(P.col[kV0] + i), 0.0, 0, on);
+                store_out(O, i, AEB_CONTACT, 0.0, 0.0, __ldg(P.col[kV0] + pi), 0.0, 0, on);
             } else if (kind == K_STOP0) {
                 store_out(O, i, AEB_STOP, 0.0, 0.0, 0.0, 0.0, 0, on);
             } else {
@@ -378,24 +380,28 @@ struct Lane32 {
             }
             return true;
         }
-        vh = tf[R_V0H * kTile + slot];
-        vl = tf[R_V0L * kTile + slot];
-        gh = tf[R_D0H * kTile + slot];
-        gl = tf[R_D0L * kTile + slot];
-        gs = tf[R_GS * kTile + slot];
-        k = tf[R_K * kTile + slot];
-        f0 = tf[R_F0 * kTile + slot];
-        f1 = tf[R_F1 * kTile + slot];
-        r0 = tf[R_R0 * kTile + slot];
-        r1 = tf[R_R1 * kTile + slot];
-        mg = tf[R_MG * kTile + slot];
-        np1 = tf[R_NP1 * kTile + slot];
-        np2 = tf[R_NP2 * kTile + slot];
-        np3 = tf[R_NP3 * kTile + slot];
-        np4 = tf[R_NP4 * kTile + slot];
-        p4 = tf[R_P4 * kTile + slot];
-        nmP = tf[R_NMP * kTile + slot];
-        nz = tf[R_NZ * kTile + slot];
+        vh = tf[R_V0H * T + slot];
+        vl = tf[R_V0L * T + slot];
+        gh = tf[R_D0H * T + slot];
+        gl = tf[R_D0L * T + slot];
+        gs = tf[R_GS * T + slot];
+        k = tf[R_K * T + slot];
+        f0 = tf[R_F0 * T + slot];
+        f1 = tf[R_F1 * T + slot];
+        r0 = tf[R_R0 * T + slot];
+        r1 = tf[R_R1 * T + slot];
+        mg = tf[R_MG * T + slot];
+        np1 = tf[R_NP1 * T + slot];
+        np2 = tf[R_NP2 * T + slot];
+        np3 = tf[R_NP3 * T + slot];
+        np4 = tf[R_NP4 * T + slot];
+        p4 = tf[R_P4 * T + slot];
+        nmP = tf[R_NMP * T + slot];
+        nz = tf[R_NZ * T + slot];
+        if (TTC) {
+            thr_h = __double2float_rn(thr);
+            thr_l = __double2float_rn(thr - (double)thr_h);
+        }
         e = 0.0f;  // a = 0 and the command is 0 before onset
         u = 0.0f;
         n = 0;
@@ -409,10 +415,10 @@ struct Lane32 {
 
 // Terminal records waiting for the binary64 refinement, per warp, field-major.
 enum { B_G0H, B_G0L, B_G1H, B_G1L, B_W0H, B_W0L, B_W1H, B_W1L, B_NF };
-enum { B_IDXLO, B_IDXHI, B_STATUS, B_N1, B_ONSET, B_NI };
+enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N1, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
-constexpr int kWarpWords = kTileWords + kBatchWords;
-constexpr size_t kSmemPerBlockAll = sizeof(float) * kWarpWords * kWarps;
+__host__ __device__ constexpr int warp_words(int T) { return (R_NF + R_NI) * T + kBatchWords; }
+__host__ __device__ constexpr size_t smem_per_block(int T) { return sizeof(float) * warp_words(T) * kWarps; }
 
 // Binary64 refinement of the last step for the warp's queued records, all 32
 // lanes at once (Sec. V-D termination; the refinement of the last step).
@@ -425,10 +431,12 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ParamsDev &
     if (j < count) {
         const uint64_t i = (uint64_t)(uint32_t)bi[B_IDXLO * 32 + j] |
                            ((uint64_t)(uint32_t)bi[B_IDXHI * 32 + j] << 32);
+        const uint64_t pi = (uint64_t)(uint32_t)bi[B_PIDXLO * 32 + j] |
+                            ((uint64_t)(uint32_t)bi[B_PIDXHI * 32 + j] << 32);
         const int status = bi[B_STATUS * 32 + j];
         const int32_t n1 = bi[B_N1 * 32 + j];
         const int32_t on = bi[B_ONSET * 32 + j];
-        const double d0 = __ldg(P.col[kD0] + i);
+        const double d0 = __ldg(P.col[kD0] + pi);
         const double x0 = d0 - ((double)bf[B_G0H * 32 + j] + (double)bf[B_G0L * 32 + j]);
         const double x1 = d0 - ((double)bf[B_G1H * 32 + j] + (double)bf[B_G1L * 32 + j]);
         const double w0 = (double)bf[B_W0H * 32 + j] + (double)bf[B_W0L * 32 + j];
@@ -456,50 +464,48 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
 {
     extern __shared__ float smem[];
     const unsigned lane = threadIdx.x & 31u;
-    float *tf = smem + (threadIdx.x >> 5) * kWarpWords;
-    int *ti = reinterpret_cast<int *>(tf + R_NF * kTile);
-    float *bf = tf + kTileWords;
+    const int T = (int)W.tile;
+    float *tf = smem + (threadIdx.x >> 5) * warp_words(T);
+    int *ti = reinterpret_cast<int *>(tf + R_NF * T);
+    float *bf = tf + (R_NF + R_NI) * T;
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
     const int32_t n_last = M.n_max - 1;
 
-    uint64_t tile_start = 0;
-    int tile_cnt = 0, cursor = 0, bcount = 0;
+    Tile tile{};
+    int cursor = 0, bcount = 0;
     bool dry = false;
     Lane32<LEAD, TTC> L;
-    uint64_t idx = 0;
+    uint64_t idx = 0, pidx = 0;
     bool active = false;
     unsigned need = kFull;
     for (;;) {
         if (need) {
             while (need) {
-                if (cursor >= tile_cnt) {
+                if (cursor >= tile.count) {
                     if (dry) {
                         if ((need >> lane) & 1u) active = false;
                         break;
                     }
-                    unsigned long long t = 0;
-                    if (lane == 0) t = atomicAdd(W.counter, 1ull);
-                    t = __shfl_sync(kFull, t, 0);
-                    const uint64_t start = (uint64_t)t * kTile;
-                    if (start >= W.n) {
+                    const Tile nt = claim_tile(W, (uint32_t)T, M.ttc_thr);
+                    if (!nt.ok) {
                         dry = true;
                         continue;
                     }
-                    tile_start = start;
-                    tile_cnt = (int)((W.n - start < (uint64_t)kTile) ? W.n - start : kTile);
+                    tile = nt;
                     cursor = 0;
                     __syncwarp();  // every lane has read its record of the previous tile
-                    prep_tile<LEAD, TTC>(M, P, tile_start, tile_cnt, tf, ti);
+                    prep_tile<LEAD, TTC>(M, P, tile.p0, tile.count, T, tf, ti);
                     __syncwarp();
                 }
                 const unsigned rank = __popc(need & lanemask_lt());
-                const bool got = ((need >> lane) & 1u) && (int)rank < tile_cnt - cursor;
+                const bool got = ((need >> lane) & 1u) && (int)rank < tile.count - cursor;
                 bool ended = false;
                 if (got) {
                     const int slot = cursor + (int)rank;
-                    idx = tile_start + slot;
+                    idx = tile.o0 + slot;
+                    pidx = tile.p0 + slot;
                     active = true;
-                    ended = L.init(M, P, O, idx, slot, tf, ti);
+                    ended = L.init(M, P, O, pidx, idx, tile.thr, slot, T, tf, ti);
                 }
                 const unsigned taken = __ballot_sync(kFull, got);
                 cursor += __popc(taken);
@@ -549,6 +555,8 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 bf[B_W1L * 32 + j] = w1l;
                 bi[B_IDXLO * 32 + j] = (int)(uint32_t)idx;
                 bi[B_IDXHI * 32 + j] = (int)(uint32_t)(idx >> 32);
+                bi[B_PIDXLO * 32 + j] = (int)(uint32_t)pidx;
+                bi[B_PIDXHI * 32 + j] = (int)(uint32_t)(pidx >> 32);
                 bi[B_STATUS * 32 + j] = status;
                 bi[B_N1 * 32 + j] = L.n + 1;
                 bi[B_ONSET * 32 + j] = L.onset();
@@ -568,8 +576,6 @@ ModelF32 to_f32(const ModelDev &m)
     f.nh6 = -(float)m.h6;
     f.ndt = -(float)m.dt;
     f.acmd = (float)m.a_cmd;
-    f.thr_h = (float)m.ttc_thr;
-    f.thr_l = (float)(m.ttc_thr - (double)f.thr_h);
     return f;
 }
 
@@ -578,24 +584,31 @@ cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, con
                      const LaunchCfg &cfg, cudaStream_t s)
 {
     auto kern = k_rollout_fp32<LEAD, TTC>;
+    const int T = w.tiles ? (int)w.tile : (cfg.tile > 0 ? cfg.tile : kTileDefault);
+    if (T < 32 || T > kTileMax || T % 32) return cudaErrorInvalidValue;
+    const size_t smem = smem_per_block(T);
     int dev = 0, sms = 0, per_sm = cfg.blocks_per_sm;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (per_sm <= 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmemPerBlockAll);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (per_sm < 1) per_sm = 1;
     }
-    const uint64_t tiles = (w.n + kTile - 1) / kTile;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+    WorkDev wt = w;
+    wt.tile = (uint32_t)T;
+    const uint64_t tiles = tiles_of(wt, (uint32_t)T);
     uint64_t blocks = (uint64_t)sms * per_sm;
     const uint64_t need_blocks = (tiles + kWarps - 1) / kWarps;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    WorkDev wt = w;
-    wt.tile = kTile;
-    kern<<<(unsigned)blocks, kThreads, kSmemPerBlockAll, s>>>(m, to_f32(m), p, o, wt);
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(m, to_f32(m), p, o, wt);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ struct NoExtra {};
 template <int CAP, bool LEAD, bool TTC>
 struct Lane64 {
     double x, v, a;
-    double d0, gs, noise, k, it;
+    double d0, gs, noise, k, it, thr;
     double mg, f0, f1, r0, r1, cap;
     int32_t n, n_b, n_delay;
     bool trig, lagged;
@@ -51,10 +51,11 @@ struct Lane64 {
     }
 
     __device__ __forceinline__ bool init(const ModelDev &M, const NoExtra &, const ParamsDev &P,
-                                         const OutDev &O, uint64_t i)
+                                         const OutDev &O, uint64_t pi, uint64_t i, double thr_job)
     {
         double f[AEB_NFIELDS];
-        load_fields(P, i, f);
+        load_fields(P, pi, f);
+        thr = thr_job;
         if (!sample_valid(f)) {
             const double nan = __longlong_as_double(0x7ff8000000000000ll);
             store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
@@ -106,7 +107,7 @@ struct Lane64 {
         const double dt = M.dt, h2 = M.h2, h6 = M.h6;
         if (TTC && !trig) {
             double gap_meas = (d0 - x) + noise;
-            if (gap_meas <= M.ttc_thr * v) {
+            if (gap_meas <= thr * v) {
                 trig = true;
                 long long nb = (long long)n + n_delay;
                 n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
@@ -166,7 +167,7 @@ struct Lane64 {
 template <int CAP, bool LEAD, bool TTC>
 __global__ void __launch_bounds__(128) k_rollout_fp64(ModelDev M, ParamsDev P, OutDev O, WorkDev W)
 {
-    rollout_driver<Lane64<CAP, LEAD, TTC>>(M, NoExtra{}, P, O, W);
+    rollout_driver<Lane64<CAP, LEAD, TTC>>(M, NoExtra{}, P, O, W, W.tile);
 }
 
 template <int CAP, bool LEAD, bool TTC>
@@ -184,7 +185,7 @@ cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, con
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    uint64_t tiles = (w.n + w.tile - 1) / w.tile;
+    const uint64_t tiles = tiles_of(w, w.tile);
     uint64_t blocks = (uint64_t)sms * per_sm;
     uint64_t need_blocks = (tiles + 3) / 4;  // one tile per warp at least
     if (need_blocks < blocks) blocks = need_blocks;

@@ -43,7 +43,8 @@ def test_struct_layouts_match_header(aeb, tmp_path):
     probe = tmp_path / "probe.c"
     structs = {"aeb_model": aeb.Model, "aeb_dist": aeb.Dist, "aeb_scenario": aeb.Scenario,
                "aeb_params": aeb.Params, "aeb_outputs": aeb.Outputs,
-               "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats}
+               "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats, "aeb_job": aeb.Job,
+               "aeb_job_stats": aeb.JobStats, "aeb_launch_config": aeb.LaunchConfig}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for cname, py in structs.items():
@@ -60,6 +61,34 @@ def test_struct_layouts_match_header(aeb, tmp_path):
         assert int(got[cname]) == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_launch_config_validation(aeb):
+    old = aeb.aeb_get_launch_config(aeb.FP32_COMP)
+    for tile, bps in ((16, 4), (48, 4), (512, 4), (64, -1), (64, 99)):
+        with pytest.raises(aeb.AebError) as e:
+            aeb.aeb_set_launch_config(aeb.FP32_COMP, tile, bps)
+        assert e.value.code == aeb.EINVAL
+    aeb.aeb_set_launch_config(aeb.FP32_COMP, 128, 5)
+    c = aeb.aeb_get_launch_config(aeb.FP32_COMP)
+    assert (c.tile, c.blocks_per_sm) == (128, 5)
+    aeb.aeb_set_launch_config(aeb.FP32_COMP, old.tile, old.blocks_per_sm)
+    with pytest.raises(aeb.AebError):
+        aeb.aeb_get_launch_config(7)
+
+
+def test_batch_rejects_bad_arguments_on_host(aeb):
+    L = aeb.lib()
+    m = aeb.model(ai.single_model())
+    p = aeb.params_struct(_cols(4))
+    o = aeb.outputs_struct(None)
+    jobs = aeb.jobs_array([(0, 0, 4, 1.0)])
+    h = C.c_void_p()
+    # no output columns / no jobs / bad threshold: rejected before any device work
+    assert L.aeb_batch_create(C.byref(m), jobs, 1, C.byref(p), 1, C.byref(o), 8, C.byref(h)) == aeb.EINVAL
+    assert L.aeb_batch_create(C.byref(m), jobs, 0, C.byref(p), 1, C.byref(o), 8, C.byref(h)) == aeb.EINVAL
+    assert L.aeb_batch_run(None, None) == aeb.EINVAL
+    L.aeb_batch_destroy(None)
 
 
 def _cols(n):
