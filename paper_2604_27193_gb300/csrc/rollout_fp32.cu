@@ -142,14 +142,32 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
     }
 }
 
+// Per-lane values read only on rare paths (piece changes, slow steps, the TTC
+// test, records) live in a column of the warp's shared slab, field-major with
+// stride 32, to keep the step loop's register budget small.
+enum {
+    L_F0, L_F1, L_R0, L_R1, L_MG, L_P4, L_GS, L_U, L_NZ, L_THRH, L_THRL,  // floats
+    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI,                                   // ints
+    L_NW
+};
+
 template <bool LEAD, bool TTC>
 struct Lane32 {
     float vh, vl, gh, gl, e;      // state: speed, gap d0 - x, actuator deviation a - u
-    float u, C, sp, eth, ethK;    // command, current piece of r(D), window threshold
-    float k, gs, f0, f1, r0, r1, mg;
-    float np1, np2, np3, np4, p4, nmP, nz, thr_h, thr_l;
-    int32_t n, ev, n_b, n_delay;  // step, next slow step, onset step, delay steps
+    float C, sp, eth, ethK;       // current piece of r(D), window threshold
+    float k, np1, np2, np3, np4, nmP;
+    int32_t n, ev;                // step, next slow step
     bool trig;
+    float *cold;                  // this lane's column: cold[field * 32]
+
+    __device__ __forceinline__ float cf(int f) const { return cold[f * 32]; }
+    __device__ __forceinline__ void set_cf(int f, float x) { cold[f * 32] = x; }
+    __device__ __forceinline__ int ci(int f) const { return __float_as_int(cold[f * 32]); }
+    __device__ __forceinline__ void set_ci(int f, int x) { cold[f * 32] = __int_as_float(x); }
+    __device__ __forceinline__ uint64_t pidx() const
+    {
+        return (uint64_t)(uint32_t)ci(L_PIDXLO) | ((uint64_t)(uint32_t)ci(L_PIDXHI) << 32);
+    }
 
     // Select the line of r(D) that is the minimum at demand D (ties: the
     // flatter line, which stays the minimum to the right), its next breakpoint
@@ -157,8 +175,9 @@ struct Lane32 {
     // D4 = -(u + p4 e) exceeds B.
     __device__ __forceinline__ void set_piece(float D)
     {
-        const float a_[4] = {0.0f, f0, r0, mg};
-        const float b_[4] = {1.0f, f1, r1, 0.0f};
+        const float u = cf(L_U), p4 = cf(L_P4);
+        const float a_[4] = {0.0f, cf(L_F0), cf(L_R0), cf(L_MG)};
+        const float b_[4] = {1.0f, cf(L_F1), cf(L_R1), 0.0f};
         float ab = 0.0f, bb = 1.0f, bv = D;
 #pragma unroll
         for (int j = 1; j < 4; ++j) {
@@ -174,7 +193,7 @@ struct Lane32 {
         for (int j = 0; j < 4; ++j)
             if (b_[j] < bb) B = fminf(B, (a_[j] - ab) / (bb - b_[j]));
         sp = bb;
-        C = (ab - bb * u) + gs;
+        C = (ab - bb * u) + cf(L_GS);
         eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
         // e decays by (1 - mP) per step; a window of K steps stays inside the
         // piece if its last step does: e (1 - mP)^(K-1) >= eth (with margin)
@@ -190,20 +209,22 @@ struct Lane32 {
     // r + g sin(theta) by the full minimum (slow steps)
     __device__ __forceinline__ float rg_full(float np) const
     {
-        const float D = -fmaf(-np, e, u);
-        const float r = fminf(fminf(D, mg), fminf(fmaf(f1, D, f0), fmaf(r1, D, r0)));
-        return r + gs;
+        const float D = -fmaf(-np, e, cf(L_U));
+        const float r = fminf(fminf(D, cf(L_MG)),
+                              fminf(fmaf(cf(L_F1), D, cf(L_F0)), fmaf(cf(L_R1), D, cf(L_R0))));
+        return r + cf(L_GS);
     }
 
     __device__ __forceinline__ int32_t onset() const
     {
-        return TTC ? (trig ? n_b : -1) : n_delay;
+        return TTC ? (trig ? ci(L_NB) : -1) : ci(L_NDELAY);
     }
 
     // Next step that must take the slow path: the onset step (if still ahead,
     // possibly the current step) or the last step.
     __device__ __forceinline__ void next_event(int32_t n_last)
     {
+        const int32_t n_b = ci(L_NB);
         ev = (trig && n_b >= n && n_b < n_last) ? n_b : n_last;
     }
 
@@ -320,8 +341,8 @@ struct Lane32 {
     __device__ __forceinline__ bool step_slow(const ModelF32 &F, int32_t n_last, float &g1h,
                                               float &g1l, float &w1h, float &w1l)
     {
-        if (n == n_b) {  // the command switches on at the start of this step
-            u = F.acmd;
+        if (n == ci(L_NB)) {  // the command switches on at the start of this step
+            set_cf(L_U, F.acmd);
             e = e - F.acmd;
         }
         const float q1 = fmaf(k * vh, vh, rg_full(np1));
@@ -336,7 +357,7 @@ struct Lane32 {
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
         if (!ended) {
             commit(g1h, g1l, w1h, w1l, en);
-            set_piece(-fmaf(-np1, e, u));
+            set_piece(-fmaf(-np1, e, cf(L_U)));
             next_event(n_last);
         }
         return ended;
@@ -346,14 +367,16 @@ struct Lane32 {
     // exact rounding error of thr * vh; braking starts n_delay steps later.
     __device__ __forceinline__ void ttc_check(const ModelF32 &F, int32_t n_last)
     {
+        const float thr_h = cf(L_THRH);
         const float p = thr_h * vh;
         const float pe = fmaf(thr_h, vh, -p);
         const float hi = gh - p;
-        const float lo = (gl + nz) - (pe + fmaf(thr_h, vl, thr_l * vh));
+        const float lo = (gl + cf(L_NZ)) - (pe + fmaf(thr_h, vl, cf(L_THRL) * vh));
         if (hi + lo <= 0.0f) {
             trig = true;
-            const long long nb = (long long)n + n_delay;
-            n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
+            const long long nb = (long long)n + ci(L_NDELAY);
+            const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
+            set_ci(L_NB, n_b);
             ev = (n_b < n_last) ? n_b : n_last;
         }
     }
@@ -365,7 +388,7 @@ struct Lane32 {
                                          const float *tf, const int *ti)
     {
         const int kind = ti[R_KIND * T + slot];
-        n_delay = ti[R_NDELAY * T + slot];
+        const int32_t n_delay = ti[R_NDELAY * T + slot];
         if (kind != K_RUN) {
             const int32_t on = TTC ? -1 : n_delay;
             if (kind == K_INVALID) {
@@ -384,29 +407,33 @@ struct Lane32 {
         vl = tf[R_V0L * T + slot];
         gh = tf[R_D0H * T + slot];
         gl = tf[R_D0L * T + slot];
-        gs = tf[R_GS * T + slot];
         k = tf[R_K * T + slot];
-        f0 = tf[R_F0 * T + slot];
-        f1 = tf[R_F1 * T + slot];
-        r0 = tf[R_R0 * T + slot];
-        r1 = tf[R_R1 * T + slot];
-        mg = tf[R_MG * T + slot];
         np1 = tf[R_NP1 * T + slot];
         np2 = tf[R_NP2 * T + slot];
         np3 = tf[R_NP3 * T + slot];
         np4 = tf[R_NP4 * T + slot];
-        p4 = tf[R_P4 * T + slot];
         nmP = tf[R_NMP * T + slot];
-        nz = tf[R_NZ * T + slot];
+        set_cf(L_GS, tf[R_GS * T + slot]);
+        set_cf(L_F0, tf[R_F0 * T + slot]);
+        set_cf(L_F1, tf[R_F1 * T + slot]);
+        set_cf(L_R0, tf[R_R0 * T + slot]);
+        set_cf(L_R1, tf[R_R1 * T + slot]);
+        set_cf(L_MG, tf[R_MG * T + slot]);
+        set_cf(L_P4, tf[R_P4 * T + slot]);
+        set_ci(L_NDELAY, n_delay);
+        set_ci(L_PIDXLO, (int)(uint32_t)pi);
+        set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
         if (TTC) {
-            thr_h = __double2float_rn(thr);
-            thr_l = __double2float_rn(thr - (double)thr_h);
+            const float thr_h = __double2float_rn(thr);
+            set_cf(L_NZ, tf[R_NZ * T + slot]);
+            set_cf(L_THRH, thr_h);
+            set_cf(L_THRL, __double2float_rn(thr - (double)thr_h));
         }
         e = 0.0f;  // a = 0 and the command is 0 before onset
-        u = 0.0f;
+        set_cf(L_U, 0.0f);
         n = 0;
         trig = !TTC;
-        n_b = TTC ? INT_MAX : n_delay;
+        set_ci(L_NB, TTC ? INT_MAX : n_delay);
         next_event(M.n_max - 1);
         set_piece(0.0f);
         return false;
@@ -417,7 +444,11 @@ struct Lane32 {
 enum { B_G0H, B_G0L, B_G1H, B_G1L, B_W0H, B_W0L, B_W1H, B_W1L, B_NF };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N1, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
-__host__ __device__ constexpr int warp_words(int T) { return (R_NF + R_NI) * T + kBatchWords; }
+constexpr int kColdWords = L_NW * 32;
+__host__ __device__ constexpr int warp_words(int T)
+{
+    return (R_NF + R_NI) * T + kBatchWords + kColdWords;
+}
 __host__ __device__ constexpr size_t smem_per_block(int T) { return sizeof(float) * warp_words(T) * kWarps; }
 
 // Binary64 refinement of the last step for the warp's queued records, all 32
@@ -469,13 +500,15 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     int *ti = reinterpret_cast<int *>(tf + R_NF * T);
     float *bf = tf + (R_NF + R_NI) * T;
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
+    float *coldw = bf + kBatchWords;
     const int32_t n_last = M.n_max - 1;
 
     Tile tile{};
     int cursor = 0, bcount = 0;
     bool dry = false;
     Lane32<LEAD, TTC> L;
-    uint64_t idx = 0, pidx = 0;
+    L.cold = coldw + lane;
+    uint64_t idx = 0;
     bool active = false;
     unsigned need = kFull;
     for (;;) {
@@ -503,9 +536,8 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 if (got) {
                     const int slot = cursor + (int)rank;
                     idx = tile.o0 + slot;
-                    pidx = tile.p0 + slot;
                     active = true;
-                    ended = L.init(M, P, O, pidx, idx, tile.thr, slot, T, tf, ti);
+                    ended = L.init(M, P, O, tile.p0 + slot, idx, tile.thr, slot, T, tf, ti);
                 }
                 const unsigned taken = __ballot_sync(kFull, got);
                 cursor += __popc(taken);
@@ -555,8 +587,8 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 bf[B_W1L * 32 + j] = w1l;
                 bi[B_IDXLO * 32 + j] = (int)(uint32_t)idx;
                 bi[B_IDXHI * 32 + j] = (int)(uint32_t)(idx >> 32);
-                bi[B_PIDXLO * 32 + j] = (int)(uint32_t)pidx;
-                bi[B_PIDXHI * 32 + j] = (int)(uint32_t)(pidx >> 32);
+                bi[B_PIDXLO * 32 + j] = L.ci(L_PIDXLO);
+                bi[B_PIDXHI * 32 + j] = L.ci(L_PIDXHI);
                 bi[B_STATUS * 32 + j] = status;
                 bi[B_N1 * 32 + j] = L.n + 1;
                 bi[B_ONSET * 32 + j] = L.onset();
