@@ -183,6 +183,35 @@ typedef struct aeb_launch_config {
 /* Opaque batched-launch plan (device tables + captured CUDA graph). */
 typedef struct aeb_batch aeb_batch;
 
+/* Serving engine configuration (the 530 ms budget of Sec. VI-F). */
+typedef struct aeb_serve_cfg {
+    aeb_precision precision;      /* rollout precision of every request               */
+    int32_t device;               /* CUDA device ordinal                              */
+    uint64_t arena_rows;          /* device rows for resident requests (admission
+                                     budget; 101 B of device memory per row)          */
+    uint64_t chunk_samples;       /* fixed chunk a request is cut into (multiple of 64) */
+    uint64_t wave_samples;        /* samples launched per wave, at most               */
+    int32_t max_waves_in_flight;  /* waves queued on the GPU at once (1..4)           */
+    int32_t sampler_threads;      /* host sampling threads (<= 0: all)                */
+    uint64_t max_request_samples; /* larger requests are rejected (<= arena_rows)     */
+} aeb_serve_cfg;
+
+/* Per-request timing, milliseconds. */
+typedef struct aeb_latency {
+    double queue_ms;   /* submit -> admitted (arena rows granted)                */
+    double sample_ms;  /* admitted -> parameters resident on the GPU            */
+    double gpu_ms;     /* resident -> statistics ready on the host              */
+    double total_ms;   /* submit -> statistics ready                            */
+} aeb_latency;
+
+/* Engine counters since creation. */
+typedef struct aeb_serve_counters {
+    uint64_t submitted, completed, cancelled, failed, rollouts, waves;
+} aeb_serve_counters;
+
+/* Opaque serving engine. */
+typedef struct aeb_server aeb_server;
+
 /* ---- entry points -------------------------------------------------------- */
 
 /* ABI version of the loaded library (AEB_ABI_VERSION when it was built). */
@@ -329,6 +358,56 @@ aeb_status aeb_set_launch_config(aeb_precision precision, const aeb_launch_confi
 aeb_status aeb_autotune(const aeb_model *model, const aeb_params *params, uint64_t n,
                         aeb_precision precision, const aeb_outputs *out, void *stream,
                         const char *cache_path, aeb_launch_config *best);
+
+/*
+ * aeb_serve_create -- start a serving engine on cfg->device for `model`
+ * (continuous batching of scenario requests, latency against
+ * the 530 ms Monte Carlo budget of Sec. VI-F).  A request is a scenario and a
+ * sample count; the engine samples it on the host (Sec. IV-C), keeps its
+ * parameters and outputs resident in a device arena, cuts it into fixed
+ * chunks and runs chunks of all admitted requests together in waves (one
+ * persistent launch each; consecutive waves overlap on two streams).  A
+ * request's statistics are the fixed-order combination of its chunks' and do
+ * not depend on what it shares waves with.
+ * Allocates the arena, pinned staging and wave buffers, and starts two host
+ * threads.  AEB_EINVAL on a bad configuration, AEB_ENOMEM if the arena cannot
+ * be allocated.
+ */
+aeb_status aeb_serve_create(const aeb_serve_cfg *cfg, const aeb_model *model, aeb_server **out);
+
+/* Queue a request; returns its ticket.  Thread-safe.  AEB_EINVAL for n == 0,
+ * n > max_request_samples or an invalid scenario. */
+aeb_status aeb_serve_submit(aeb_server *srv, const aeb_scenario *scenario, uint64_t n,
+                            uint64_t *ticket);
+
+/*
+ * Wait up to timeout_ms (0: do not wait, < 0: no limit) for a request.  On
+ * AEB_OK the statistics and latency are written and the ticket is released.
+ * AEB_EAGAIN (timeout_ms == 0) or AEB_ETIMEOUT if still running,
+ * AEB_ECANCELLED if cancelled, AEB_EINVAL for an unknown ticket.  Thread-safe.
+ */
+aeb_status aeb_serve_poll(aeb_server *srv, uint64_t ticket, int32_t timeout_ms,
+                          aeb_job_stats *stats, aeb_latency *lat);
+
+/* Cancel a request not yet admitted (an admitted one runs to the end and its
+ * result is discarded).  AEB_EINVAL for an unknown ticket. */
+aeb_status aeb_serve_cancel(aeb_server *srv, uint64_t ticket);
+
+/* Engine counters (thread-safe snapshot). */
+aeb_status aeb_serve_counters_get(aeb_server *srv, aeb_serve_counters *out);
+
+/* Stop the engine after the work in flight, release everything (NULL: no-op). */
+void aeb_serve_destroy(aeb_server *srv);
+
+/*
+ * aeb_pipe_peaks -- measured throughput of the arithmetic pipes the rollout
+ * kernels are bound by (no counterpart in the paper; the roofline denominators
+ * of Sec. V-E's compute-bound kernels): binary32 FMA and binary64 FMA in
+ * TFLOP/s (an FMA counts two), binary64 add in Tops/s, from many independent
+ * dependency chains per thread.  Synchronous; ~10 ms of GPU time.
+ */
+aeb_status aeb_pipe_peaks(double *fp32_fma_tflops, double *fp64_fma_tflops, double *fp64_add_tops,
+                          void *stream);
 
 #ifdef __cplusplus
 }

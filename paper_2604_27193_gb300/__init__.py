@@ -94,6 +94,22 @@ class LaunchConfig(C.Structure):
     _fields_ = [("tile", C.c_int32), ("blocks_per_sm", C.c_int32)]
 
 
+class ServeCfg(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("arena_rows", C.c_uint64),
+                ("chunk_samples", C.c_uint64), ("wave_samples", C.c_uint64),
+                ("max_waves_in_flight", C.c_int32), ("sampler_threads", C.c_int32),
+                ("max_request_samples", C.c_uint64)]
+
+
+class Latency(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("queue_ms", "sample_ms", "gpu_ms", "total_ms")]
+
+
+class ServeCounters(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "cancelled", "failed",
+                                          "rollouts", "waves")]
+
+
 STATS_BYTES = C.sizeof(Stats)
 JOB_STATS_BYTES = C.sizeof(JobStats)
 
@@ -136,9 +152,19 @@ def lib():
             L.aeb_set_launch_config.argtypes = [C.c_int32, P(LaunchConfig)]
             L.aeb_autotune.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32, P(Outputs),
                                        C.c_void_p, C.c_char_p, P(LaunchConfig)]
+            L.aeb_serve_create.argtypes = [P(ServeCfg), P(Model), P(C.c_void_p)]
+            L.aeb_serve_submit.argtypes = [C.c_void_p, P(Scenario), C.c_uint64, P(C.c_uint64)]
+            L.aeb_serve_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, P(JobStats),
+                                         P(Latency)]
+            L.aeb_serve_cancel.argtypes = [C.c_void_p, C.c_uint64]
+            L.aeb_serve_counters_get.argtypes = [C.c_void_p, P(ServeCounters)]
+            L.aeb_serve_destroy.argtypes = [C.c_void_p]
+            L.aeb_serve_destroy.restype = None
             for fn in ("aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate",
                        "aeb_batch_create", "aeb_batch_run", "aeb_rollout_batched",
-                       "aeb_get_launch_config", "aeb_set_launch_config", "aeb_autotune"):
+                       "aeb_get_launch_config", "aeb_set_launch_config", "aeb_autotune",
+                       "aeb_serve_create", "aeb_serve_submit", "aeb_serve_poll",
+                       "aeb_serve_cancel", "aeb_serve_counters_get"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != 1:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -328,6 +354,64 @@ def aeb_autotune(m, params: dict, n: int, precision: int, out: dict, stream=None
                               _stream(stream), cache_path.encode() if cache_path else None,
                               C.byref(c)))
     return c
+
+
+class Server:
+    """aeb_serve_create / submit / poll / cancel / destroy."""
+
+    def __init__(self, m, precision: int = FP32_COMP, device: int = 0,
+                 arena_rows: int = 1 << 22, chunk_samples: int = 1 << 18,
+                 wave_samples: int = 1 << 21, max_waves_in_flight: int = 2,
+                 sampler_threads: int = 0, max_request_samples: int = 1_000_000):
+        cfg = ServeCfg(precision, device, arena_rows, chunk_samples, wave_samples,
+                       max_waves_in_flight, sampler_threads, max_request_samples)
+        self._h = C.c_void_p()
+        ms = model(m)
+        _check(lib().aeb_serve_create(C.byref(cfg), C.byref(ms), C.byref(self._h)))
+
+    def submit(self, sc, n: int) -> int:
+        t = C.c_uint64()
+        ss = scenario(sc)
+        _check(lib().aeb_serve_submit(self._h, C.byref(ss), n, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(status, JobStats, Latency); status OK, EAGAIN, ETIMEOUT or ECANCELLED."""
+        st, lat = JobStats(), Latency()
+        code = lib().aeb_serve_poll(self._h, ticket, timeout_ms, C.byref(st), C.byref(lat))
+        if code not in (OK, EAGAIN, ETIMEOUT, ECANCELLED):
+            _check(code)
+        return code, st, lat
+
+    def cancel(self, ticket: int):
+        _check(lib().aeb_serve_cancel(self._h, ticket))
+
+    def counters(self) -> ServeCounters:
+        c = ServeCounters()
+        _check(lib().aeb_serve_counters_get(self._h, C.byref(c)))
+        return c
+
+    def close(self):
+        if self._h:
+            lib().aeb_serve_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def aeb_pipe_peaks(stream=None):
+    """Measured (fp32 FMA TFLOP/s, fp64 FMA TFLOP/s, fp64 add Tops/s)."""
+    L = lib()
+    fn = L.aeb_pipe_peaks
+    fn.argtypes = [C.POINTER(C.c_double)] * 3 + [C.c_void_p]
+    fn.restype = C.c_int32
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(fn(C.byref(a), C.byref(b), C.byref(c), _stream(stream)))
+    return a.value, b.value, c.value
 
 
 def job_stats_from_buffer(buf, n_jobs: int):

@@ -26,8 +26,9 @@ CU_SOURCES = {
     "rollout_fp32.cu": [],
     "reduce.cu": [],
     "reduce_noalloc.cu": [],
+    "peaks.cu": ["-fmad=true"],
 }
-CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp"]
+CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp"]
 HEADERS = ["aeb_internal.h", "rollout_common.cuh", "host_util.h"]
 
 

@@ -44,7 +44,9 @@ def test_struct_layouts_match_header(aeb, tmp_path):
     structs = {"aeb_model": aeb.Model, "aeb_dist": aeb.Dist, "aeb_scenario": aeb.Scenario,
                "aeb_params": aeb.Params, "aeb_outputs": aeb.Outputs,
                "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats, "aeb_job": aeb.Job,
-               "aeb_job_stats": aeb.JobStats, "aeb_launch_config": aeb.LaunchConfig}
+               "aeb_job_stats": aeb.JobStats, "aeb_launch_config": aeb.LaunchConfig,
+               "aeb_serve_cfg": aeb.ServeCfg, "aeb_latency": aeb.Latency,
+               "aeb_serve_counters": aeb.ServeCounters}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for cname, py in structs.items():
@@ -89,6 +91,23 @@ def test_batch_rejects_bad_arguments_on_host(aeb):
     assert L.aeb_batch_create(C.byref(m), jobs, 0, C.byref(p), 1, C.byref(o), 8, C.byref(h)) == aeb.EINVAL
     assert L.aeb_batch_run(None, None) == aeb.EINVAL
     L.aeb_batch_destroy(None)
+
+
+def test_serve_rejects_bad_config_on_host(aeb):
+    L = aeb.lib()
+    m = aeb.model(ai.single_model())
+    h = C.c_void_p()
+    good = dict(precision=1, device=0, arena_rows=1 << 20, chunk_samples=1 << 16,
+                wave_samples=1 << 20, max_waves_in_flight=2, sampler_threads=1,
+                max_request_samples=1 << 20)
+    for k, v in (("chunk_samples", 100), ("chunk_samples", 0), ("max_waves_in_flight", 0),
+                 ("max_waves_in_flight", 9), ("arena_rows", 0), ("precision", 5),
+                 ("max_request_samples", 1 << 21), ("wave_samples", 1 << 10)):
+        cfg = aeb.ServeCfg(**dict(good, **{k: v}))
+        assert L.aeb_serve_create(C.byref(cfg), C.byref(m), C.byref(h)) == aeb.EINVAL, k
+    assert L.aeb_serve_submit(None, None, 1, None) == aeb.EINVAL
+    assert L.aeb_serve_poll(None, 1, 0, None, None) == aeb.EINVAL
+    L.aeb_serve_destroy(None)
 
 
 def _cols(n):
