@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-grid and TTC-sweep lines")
     return ap.parse_args()
 
 
@@ -175,6 +177,58 @@ def serve_run(aeb, m, seconds: float, rate: float):
             "offered_rollouts_per_s": rollouts / seconds, "waves": int(c1.waves - c0.waves),
             "precision": "fp32-compensated",
             "note": "rollouts_per_s is bounded by the offered load, not by the GPU"}
+
+
+def batched_run(aeb, torch, dev, stream):
+    """The scenario-grid workload: 4,096 scenarios (16 x 16 x 16 means) with
+    per-scenario N log-uniform in [1e3, 6.4e4] (~6e7 rollouts), FP32-compensated,
+    one captured graph per run (persistent launch + per-scenario reductions)."""
+    m = ai.single_model()
+    grid = ai.grid_scenarios(seed=2)
+    total = sum(n for _, n in grid)
+    host = aeb.alloc_params(total, device="cpu", pin=True)
+    off = 0
+    jobs = []
+    for k, (sc, n) in enumerate(grid):
+        aeb.aeb_sample_params(m, sc, 0, n, {f: host[f][off:off + n] for f in ai.FIELDS})
+        jobs.append((off, off, n, 0.0))
+        off += n
+    P = {f: host[f].to(dev, non_blocking=True) for f in ai.FIELDS}
+    O = aeb.alloc_outputs(total, device=dev, which=("status", "x_ref", "v_imp", "n_steps"))
+    S = torch.empty(aeb.JOB_STATS_BYTES * len(jobs), dtype=torch.uint8, device=dev)
+    plan = aeb.BatchPlan(m, jobs, P, aeb.FP32_COMP, O, S)
+    plan.run(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        plan.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.close()
+    ms = e0.elapsed_time(e1) / reps
+    st = aeb.job_stats_from_buffer(S, len(jobs))
+    assert sum(j.n for j in st) == total
+    return {"scenarios": len(jobs), "rollouts": int(total), "ms_per_run": ms,
+            "rollouts_per_s": total / (ms / 1e3), "launch": "one CUDA graph per run",
+            "precision": "fp32-compensated"}
+
+
+def sweep_run(aeb):
+    """TTC-threshold sweep: 256 thresholds in [0.5, 4.0] s x 64 scenarios x
+    1e5 samples (~1.64e9 rollouts), FP32-compensated, through aeb_ttc_sweep
+    (host sampling, upload, batched launches, pooled Wilson intervals)."""
+    m = ai.ttc_model()
+    scen = ai.ttc_scenarios(64, seed=4)
+    thr = ai.ttc_thresholds(256)
+    t0 = time.perf_counter()
+    res = aeb.aeb_ttc_sweep(m, scen, 100_000, thr, aeb.FP32_COMP)
+    dt = time.perf_counter() - t0
+    total = sum(r.n for r in res)
+    pick = {f"{r.threshold:.2f}": [r.p_contact, r.ci_lo, r.ci_hi] for r in res[::51]}
+    return {"rollouts": int(total), "seconds": dt, "rollouts_per_s": total / dt,
+            "p_contact_ci95_at": pick, "precision": "fp32-compensated"}
 
 
 def config(args, world):
@@ -320,6 +374,13 @@ def main():
 
     peaks = aeb.aeb_pipe_peaks(stream)
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
+    del P, O
+    torch.cuda.empty_cache()
+    batched = sweep = None
+    if not args.no_extras:
+        batched = batched_run(aeb, torch, dev, stream)
+        torch.cuda.empty_cache()
+        sweep = sweep_run(aeb)
 
     if rank != 0:
         if dist:
@@ -346,6 +407,8 @@ def main():
                                 "how": "aeb_pipe_peaks: 8 independent FMA/add chains per thread"},
         "fp64_plain": fp64,
         "serving": serving,
+        "batched_grid": batched,
+        "ttc_sweep": sweep,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
         "steps_per_rollout": steps_per_launch / N,

@@ -212,6 +212,15 @@ typedef struct aeb_serve_counters {
 /* Opaque serving engine. */
 typedef struct aeb_server aeb_server;
 
+/* Collision probability at one TTC threshold, pooled over the scenarios
+ * (Sec. VI-C, Eq. 19 with the TTC = H0 / v criterion). */
+typedef struct aeb_sweep_result {
+    double threshold;
+    uint64_t n, n_contact, n_stop, n_horizon, n_invalid;
+    double p_contact;      /* n_contact / (n - n_invalid)                       */
+    double ci_lo, ci_hi;   /* 95 % Wilson score interval of p_contact           */
+} aeb_sweep_result;
+
 /* ---- entry points -------------------------------------------------------- */
 
 /* ABI version of the loaded library (AEB_ABI_VERSION when it was built). */
@@ -398,6 +407,27 @@ aeb_status aeb_serve_counters_get(aeb_server *srv, aeb_serve_counters *out);
 
 /* Stop the engine after the work in flight, release everything (NULL: no-op). */
 void aeb_serve_destroy(aeb_server *srv);
+
+/*
+ * aeb_ttc_sweep -- collision probability against the TTC trigger threshold
+ * (TTC = H0 / v_rel, Sec. VI-C).  Samples n_per_scenario
+ * parameter sets of every scenario once on the host (Sec. IV-C), keeps them
+ * resident, and runs every (threshold, scenario) pair as a job of batched
+ * launches (thresholds in chunks, all reading the same parameter rows) with
+ * model->trigger forced to AEB_TRIGGER_TTC.
+ *   per_threshold  host, n_thr entries: pooled counts, p, Wilson 95 % interval
+ *   per_job        host, n_thr * n_scen entries (threshold-major) or NULL
+ * Synchronous; allocates and frees its device buffers (about
+ * 80 B x n_scen x n_per_scenario for parameters plus up to 4.5 GB of outputs).
+ */
+aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *scenarios, uint32_t n_scen,
+                         uint64_t n_per_scenario, const double *thresholds, uint32_t n_thr,
+                         aeb_precision precision, aeb_sweep_result *per_threshold,
+                         aeb_job_stats *per_job, void *stream);
+
+/* Wilson score interval of k successes in n trials at normal quantile z
+ * (z = 1.959963984540054 for 95 %).  n == 0 gives [0, 1]. */
+aeb_status aeb_wilson(uint64_t k, uint64_t n, double z, double *lo, double *hi);
 
 /*
  * aeb_pipe_peaks -- measured throughput of the arithmetic pipes the rollout

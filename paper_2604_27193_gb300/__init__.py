@@ -110,6 +110,12 @@ class ServeCounters(C.Structure):
                                           "rollouts", "waves")]
 
 
+class SweepResult(C.Structure):
+    _fields_ = [("threshold", C.c_double)] + \
+        [(n, C.c_uint64) for n in ("n", "n_contact", "n_stop", "n_horizon", "n_invalid")] + \
+        [(n, C.c_double) for n in ("p_contact", "ci_lo", "ci_hi")]
+
+
 STATS_BYTES = C.sizeof(Stats)
 JOB_STATS_BYTES = C.sizeof(JobStats)
 
@@ -401,6 +407,36 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def aeb_ttc_sweep(m, scenarios, n_per_scenario: int, thresholds, precision: int = FP32_COMP,
+                  per_job: bool = False, stream=None):
+    """Per-threshold SweepResult list (and per-(threshold, scenario) JobStats)."""
+    L = lib()
+    fn = L.aeb_ttc_sweep
+    fn.argtypes = [C.POINTER(Model), C.POINTER(Scenario), C.c_uint32, C.c_uint64,
+                   C.POINTER(C.c_double), C.c_uint32, C.c_int32, C.POINTER(SweepResult),
+                   C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int32
+    ms = model(m)
+    sc = (Scenario * len(scenarios))(*[scenario(s) for s in scenarios])
+    th = (C.c_double * len(thresholds))(*[float(t) for t in thresholds])
+    res = (SweepResult * len(thresholds))()
+    jobs = (JobStats * (len(thresholds) * len(scenarios)))() if per_job else None
+    _check(fn(C.byref(ms), sc, len(scenarios), n_per_scenario, th, len(thresholds), precision,
+              res, C.cast(jobs, C.c_void_p) if jobs is not None else None, _stream(stream)))
+    return (list(res), list(jobs)) if per_job else list(res)
+
+
+def aeb_wilson(k: int, n: int, z: float = 1.959963984540054):
+    L = lib()
+    fn = L.aeb_wilson
+    fn.argtypes = [C.c_uint64, C.c_uint64, C.c_double, C.POINTER(C.c_double),
+                   C.POINTER(C.c_double)]
+    fn.restype = C.c_int32
+    lo, hi = C.c_double(), C.c_double()
+    _check(fn(k, n, z, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
 
 
 def aeb_pipe_peaks(stream=None):

@@ -28,7 +28,7 @@ CU_SOURCES = {
     "reduce_noalloc.cu": [],
     "peaks.cu": ["-fmad=true"],
 }
-CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp"]
+CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp", "sweep.cpp"]
 HEADERS = ["aeb_internal.h", "rollout_common.cuh", "host_util.h"]
 
 

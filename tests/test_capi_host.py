@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(aeb, tmp_path):
                "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats, "aeb_job": aeb.Job,
                "aeb_job_stats": aeb.JobStats, "aeb_launch_config": aeb.LaunchConfig,
                "aeb_serve_cfg": aeb.ServeCfg, "aeb_latency": aeb.Latency,
-               "aeb_serve_counters": aeb.ServeCounters}
+               "aeb_serve_counters": aeb.ServeCounters, "aeb_sweep_result": aeb.SweepResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for cname, py in structs.items():
@@ -108,6 +108,11 @@ def test_serve_rejects_bad_config_on_host(aeb):
     assert L.aeb_serve_submit(None, None, 1, None) == aeb.EINVAL
     assert L.aeb_serve_poll(None, 1, 0, None, None) == aeb.EINVAL
     L.aeb_serve_destroy(None)
+
+
+@pytest.mark.parametrize("k,n", [(0, 10), (3, 10), (10, 10), (37, 1000), (5000, 100000), (0, 0)])
+def test_library_wilson_matches_oracle(aeb, oracle_mod, k, n):
+    assert np.allclose(aeb.aeb_wilson(k, n), oracle_mod.wilson(k, n), rtol=0, atol=1e-15)
 
 
 def _cols(n):
