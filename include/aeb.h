@@ -425,6 +425,17 @@ aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *scenarios, 
                          aeb_precision precision, aeb_sweep_result *per_threshold,
                          aeb_job_stats *per_job, void *stream);
 
+/*
+ * aeb_stats_merge / aeb_job_stats_merge -- add the statistics of another
+ * disjoint set of samples into `acc` (host memory; the exchange step when the
+ * samples of one workload are split across GPUs or calls).  Counts and
+ * histograms add exactly; sums add in call order, so merging the parts in a
+ * fixed order (e.g. rank order) gives the same bits every time.  aeb_stats
+ * parts must share the histogram spec (AEB_EINVAL otherwise).
+ */
+aeb_status aeb_stats_merge(aeb_stats *acc, const aeb_stats *part);
+aeb_status aeb_job_stats_merge(aeb_job_stats *acc, const aeb_job_stats *part);
+
 /* Wilson score interval of k successes in n trials at normal quantile z
  * (z = 1.959963984540054 for 95 %).  n == 0 gives [0, 1]. */
 aeb_status aeb_wilson(uint64_t k, uint64_t n, double z, double *lo, double *hi);

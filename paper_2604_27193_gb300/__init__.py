@@ -428,6 +428,25 @@ def aeb_ttc_sweep(m, scenarios, n_per_scenario: int, thresholds, precision: int 
     return (list(res), list(jobs)) if per_job else list(res)
 
 
+def aeb_stats_merge(acc: Stats, part: Stats) -> Stats:
+    """Add `part` into `acc` (host; counts and histograms exact)."""
+    fn = lib().aeb_stats_merge
+    fn.argtypes = [C.POINTER(Stats), C.POINTER(Stats)]
+    fn.restype = C.c_int32
+    _check(fn(C.byref(acc), C.byref(part)))
+    return acc
+
+
+def empty_stats(hist: HistSpec | None = None) -> Stats:
+    """Identity element of aeb_stats_merge for a histogram spec."""
+    h = hist or hist_spec()
+    st = Stats()
+    st.min_d = st.min_v = float("inf")
+    st.max_d = st.max_v = float("-inf")
+    st.lo_d, st.w_d, st.lo_v, st.w_v = h.lo_d, h.w_d, h.lo_v, h.w_v
+    return st
+
+
 def aeb_wilson(k: int, n: int, z: float = 1.959963984540054):
     L = lib()
     fn = L.aeb_wilson

@@ -26,6 +26,52 @@ extern "C" aeb_status aeb_wilson(uint64_t k, uint64_t n, double z, double *lo, d
     return AEB_OK;
 }
 
+namespace {
+
+template <class S>
+void merge_common(S &a, const S &b)
+{
+    a.n += b.n;
+    a.n_stop += b.n_stop;
+    a.n_contact += b.n_contact;
+    a.n_horizon += b.n_horizon;
+    a.n_invalid += b.n_invalid;
+    a.steps += b.steps;
+    a.sum_d += b.sum_d;
+    a.sumsq_d += b.sumsq_d;
+    a.sum_v += b.sum_v;
+    a.sumsq_v += b.sumsq_v;
+    a.min_d = std::fmin(a.min_d, b.min_d);
+    a.max_d = std::fmax(a.max_d, b.max_d);
+    a.min_v = std::fmin(a.min_v, b.min_v);
+    a.max_v = std::fmax(a.max_v, b.max_v);
+}
+
+}  // namespace
+
+extern "C" aeb_status aeb_stats_merge(aeb_stats *acc, const aeb_stats *part)
+{
+    aeb::clear_error();
+    if (!acc || !part) return aeb::fail(AEB_EINVAL, "aeb_stats_merge: NULL argument");
+    if (acc->lo_d != part->lo_d || acc->w_d != part->w_d || acc->lo_v != part->lo_v ||
+        acc->w_v != part->w_v)
+        return aeb::fail(AEB_EINVAL, "aeb_stats_merge: histogram specs differ");
+    merge_common(*acc, *part);
+    for (int j = 0; j < AEB_NBINS; ++j) {
+        acc->hist_d[j] += part->hist_d[j];
+        acc->hist_v[j] += part->hist_v[j];
+    }
+    return AEB_OK;
+}
+
+extern "C" aeb_status aeb_job_stats_merge(aeb_job_stats *acc, const aeb_job_stats *part)
+{
+    aeb::clear_error();
+    if (!acc || !part) return aeb::fail(AEB_EINVAL, "aeb_job_stats_merge: NULL argument");
+    merge_common(*acc, *part);
+    return AEB_OK;
+}
+
 extern "C" aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *scenarios,
                                     uint32_t n_scen, uint64_t n_per, const double *thresholds,
                                     uint32_t n_thr, aeb_precision precision,
