@@ -46,6 +46,9 @@ FLOPS_PER_STEP = 73
 SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
+# DRAM bytes per sample of the FP32 rollout kernel, from one ncu capture at
+# N = 2e6 (183.7 MB per launch); traffic grows in proportion to the samples.
+FP32_TRAFFIC_BYTES_PER_SAMPLE = 183.657216e6 / 2e6
 
 
 def parse():
@@ -397,7 +400,10 @@ def main():
         "clocks": clocks,
         "roofline": {"bound": "alu", "kernel": "k_rollout_fp32", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": FP32_TRAFFIC_BYTES_PER_SAMPLE * N if N >= 2_000_000 else None,
+                     "traffic_source": "ncu dram__bytes_read+write of k_rollout_fp32 at N=2e6 "
+                                       "(profiles/rollout_fp32_single_scenario_n2e6.md), "
+                                       "scaled by samples",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts, max clock)",
                      "flops_per_launch": steps_per_launch * FLOPS_PER_STEP,
                      "launch_ms": roll_ms},
