@@ -40,10 +40,13 @@
 // lane queues its terminal state in the warp's shared slab, and the warp refines
 // 32 queued rollouts at once.
 //
-// Steps that need more than the piece formula take a slow path: the brake-onset
-// step, the last step before the horizon, and a step that crosses a breakpoint.
-// The next such step is kept per lane, so the fast path tests one integer and
-// one float per step.
+// Steps run in windows of up to K = 8 with no test in between.  A lane's
+// window ends before its next event (brake onset, the last step before the
+// horizon, a step that crosses a breakpoint of r(D)); lanes of a warp with
+// shorter windows run the same window code masked, so a lane close to an event
+// does not hold up the others.  Brake onset is a change of state between two
+// steps (new command, new piece); only the breakpoint-crossing step and the
+// last step take a slow path that evaluates the full minimum per stage.
 #include <climits>
 
 #include "rollout_common.cuh"
@@ -280,25 +283,42 @@ struct Lane32 {
         return ended;
     }
 
-    // Whether the next K steps may run as one window: no slow step among them
-    // and the trigger (if any) already fired.
-    __device__ __forceinline__ bool window_ok() const
+    // How many steps (1 .. K) may run as one window from here: none of them
+    // a slow step, the trigger (if any) already fired, and the piece of r(D)
+    // valid for each (the actuator deviation e, which decays by the factor
+    // q = 1 - mP per step, stays >= eth at the start of every step; the 1e-6
+    // margin covers the rounding of the decays).
+    __device__ __forceinline__ int window_len() const
     {
-        return (!TTC || trig) && n + AEB_FP32_WINDOW <= ev && !(e < ethK);
+        if (TTC && !trig) return 1;
+        const int32_t room = ev - n;  // >= 1: a lane at its event takes the slow path
+        int len = room < AEB_FP32_WINDOW ? (int)room : AEB_FP32_WINDOW;
+        if (e < ethK) {  // close to a breakpoint (eth > 0 here)
+            const float q = 1.0f + nmP, m = eth * 1.000001f;
+            int lb = 1;
+            if (q > 0.0f && q < 1.0f) lb = (e * (q * q * q) >= m) ? 4 : ((e * q >= m) ? 2 : 1);
+            len = len < lb ? len : lb;
+        }
+        return len;
     }
 
-    // K fast steps with no termination test in between.  Within a few
-    // milliseconds a stop leaves v <= 0 and a contact leaves g <= 0 (a contact
-    // at near-zero speed turns into v <= 0), so the state after the window
-    // shows whether the rollout ended inside it; if so the window is undone and
-    // replayed one checked step at a time, which reproduces the same
-    // arithmetic and finds the terminating step.
-    __device__ __forceinline__ bool step_window(const ModelF32 &F, float &g1h, float &g1l,
+    // `len` fast steps (FULL: len = K) with no termination test in between.
+    // Within a few milliseconds a stop leaves v <= 0 and a contact leaves
+    // g <= 0 (a contact at near-zero speed turns into v <= 0), so the state
+    // after the window shows whether the rollout ended inside it; if so the
+    // window is undone and replayed one checked step at a time, which
+    // reproduces the same arithmetic and finds the terminating step.  Lanes
+    // of a warp with different lengths run the same window code, each masked
+    // off after its own length.
+    template <bool FULL>
+    __device__ __forceinline__ bool step_window(const ModelF32 &F, int len, float &g1h, float &g1l,
                                                 float &w1h, float &w1l)
     {
+        if (FULL) len = AEB_FP32_WINDOW;
         const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
 #pragma unroll
         for (int j = 0; j < AEB_FP32_WINDOW; ++j) {
+            if (!FULL && j >= len) break;
             const float S = sp * e;
             const float q1 = fmaf(k * vh, vh, fmaf(S, np1, C));
             const float v2 = fmaf(F.nh2, q1, vh);
@@ -322,22 +342,28 @@ struct Lane32 {
             gl = gl0;
             e = e0;
 #pragma unroll 1
-            for (int j = 0; j < AEB_FP32_WINDOW; ++j)
+            for (int j = 0; j < len; ++j)
                 if (step_fast(F, g1h, g1l, w1h, w1l)) return true;
             return false;
         }
-        n += AEB_FP32_WINDOW;
+        n += len;
         return false;
     }
 
-    // Whether the next step may take the fast path.
-    __device__ __forceinline__ bool fast_next() const
+    // Brake onset (the command switches on at the start of step n_b): the
+    // actuator deviation jumps by -a_cmd and the piece of r(D) is selected at
+    // the step's first-stage demand; the step itself then runs as a fast step.
+    __device__ __forceinline__ void onset_event(const ModelF32 &F, int32_t n_last)
     {
-        return n != ev && !(e < eth) && (!TTC || trig);
+        set_cf(L_U, F.acmd);
+        e = e - F.acmd;
+        set_piece(-fmaf(-np1, e, F.acmd));
+        ev = n_last;
     }
 
-    // The brake-onset step, a step crossing a breakpoint of r(D), or the last
-    // step before the horizon: full minimum for r, then re-select the piece.
+    // A step crossing a breakpoint of r(D), or the last step before the
+    // horizon (which may also be the onset step): full minimum for r, then
+    // re-select the piece.
     __device__ __forceinline__ bool step_slow(const ModelF32 &F, int32_t n_last, float &g1h,
                                               float &g1l, float &w1h, float &w1l)
     {
@@ -549,21 +575,24 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
             }
         }
 
-        // ---- up to two RK4 steps (Sec. IV-D) per lane ----
+        // ---- one window of up to K RK4 steps (Sec. IV-D) per lane ----
         bool ended = false;
         float g1h, g1l, w1h, w1l;
         if (TTC && active && !L.trig) L.ttc_check(F, n_last);
+        const bool onset = active && L.n == L.ev && L.n < n_last;
+        if (__any_sync(kFull, onset)) {  // warp-uniform: once per rollout
+            if (onset) L.onset_event(F, n_last);
+        }
         const bool slow = active && ((L.n == L.ev) || (L.e < L.eth));
         if (__any_sync(kFull, slow)) {  // warp-uniform: rare
             if (slow) ended = L.step_slow(F, n_last, g1h, g1l, w1h, w1l);
         }
-        if (active && !slow) {
-            if (L.window_ok()) {
-                ended = L.step_window(F, g1h, g1l, w1h, w1l);
-            } else {
-                ended = L.step_fast(F, g1h, g1l, w1h, w1l);
-                if (!ended && L.fast_next()) ended = L.step_fast(F, g1h, g1l, w1h, w1l);
-            }
+        const bool win = active && !slow;
+        const int len = win ? L.window_len() : AEB_FP32_WINDOW;
+        if (__all_sync(kFull, len == AEB_FP32_WINDOW)) {
+            if (win) ended = L.template step_window<true>(F, len, g1h, g1l, w1h, w1l);
+        } else {
+            if (win) ended = L.template step_window<false>(F, len, g1h, g1l, w1h, w1l);
         }
         const unsigned endm = __ballot_sync(kFull, ended);
         if (endm) {
