@@ -1,9 +1,11 @@
 """Build ``libaeb.so`` in-tree for sm_103a (GB300).
 
 Every translation unit is compiled in parallel, then linked with nvcc.  The
-binary64 rollout kernel is compiled with ``-fmad=false`` (no fused
-multiply-add may be formed), host code with ``-ffp-contract=off``; nothing is
-built with fast-math.  Set ``AEB_PTXAS_VERBOSE=1`` to print ptxas resource
+rollout kernels are compiled with ``-fmad=false`` (no fused multiply-add is
+formed unless the source writes ``fma``): the binary64 kernel so that it
+mirrors the oracle's operation order, the binary32 kernel so that a replayed
+window repeats the window's arithmetic exactly.  Host code is compiled with
+``-ffp-contract=off``; nothing is built with fast-math.  Set ``AEB_PTXAS_VERBOSE=1`` to print ptxas resource
 usage of the kernels.
 """
 from __future__ import annotations
@@ -23,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = {
     "rollout_fp64.cu": ["-fmad=false"],
-    "rollout_fp32.cu": [],
+    "rollout_fp32.cu": ["-fmad=false"],
     "reduce.cu": [],
     "reduce_noalloc.cu": [],
     "peaks.cu": ["-fmad=true"],

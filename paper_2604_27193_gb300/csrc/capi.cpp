@@ -165,7 +165,7 @@ aeb_status scratch_for(cudaStream_t s, size_t bytes, void **out)
 }
 
 std::mutex g_cfg_mu;
-LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 64}};
+LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 32}};
 
 aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
                         aeb_precision precision, const OutDev &od, cudaStream_t s)

@@ -54,7 +54,7 @@
 namespace aeb {
 namespace {
 
-constexpr int kTileDefault = 64;  // samples per warp tile unless configured
+constexpr int kTileDefault = 32;  // samples per warp tile unless configured
 constexpr int kTileMax = 256;
 constexpr int kWarps = 4;      // warps per block
 constexpr int kThreads = 32 * kWarps;
@@ -241,10 +241,9 @@ struct Lane32 {
         // position increment formed with dt instead would scale distance
         // against speed by the ratio of two independently rounded constants
         // (a systematic ~5e-8 relative error in every stopping distance).
-        const float dv = F.nh6 * fmaf(2.0f, q2 + q3, q1 + q4);
         const float dx = fmaf(F.dt, vl, F.h6 * fmaf(2.0f, v2 + v3, vh + v4));
         // Fast2Sum of (hi, lo + increment) keeps each pair normalised
-        const float tv = dv + vl;
+        const float tv = fmaf(F.nh6, fmaf(2.0f, q2 + q3, q1 + q4), vl);
         w1h = vh + tv;
         w1l = tv - (w1h - vh);
         const float tg = gl - dx;
@@ -305,16 +304,19 @@ struct Lane32 {
     // `len` fast steps (FULL: len = K) with no termination test in between.
     // Within a few milliseconds a stop leaves v <= 0 and a contact leaves
     // g <= 0 (a contact at near-zero speed turns into v <= 0), so the state
-    // after the window shows whether the rollout ended inside it; if so the
-    // window is undone and replayed one checked step at a time, which
-    // reproduces the same arithmetic and finds the terminating step.  Lanes
-    // of a warp with different lengths run the same window code, each masked
-    // off after its own length.
+    // after the window shows whether the rollout ended inside it.  If so the
+    // lane's state goes back to the window's start and the function returns
+    // true: the warp queues the window and later replays it, one checked
+    // step at a time, for 32 rollouts at once (`flush_batch`).  The replay
+    // reproduces the same arithmetic (this file is compiled without FMA
+    // contraction) and so finds the terminating step.  Lanes of a warp with
+    // different lengths run the same window code, each masked off after its
+    // own length.
     template <bool FULL>
-    __device__ __forceinline__ bool step_window(const ModelF32 &F, int len, float &g1h, float &g1l,
-                                                float &w1h, float &w1l)
+    __device__ __forceinline__ bool step_window(const ModelF32 &F, int len)
     {
         if (FULL) len = AEB_FP32_WINDOW;
+        float g1h, g1l, w1h, w1l;
         const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
 #pragma unroll
         for (int j = 0; j < AEB_FP32_WINDOW; ++j) {
@@ -341,10 +343,7 @@ struct Lane32 {
             gh = gh0;
             gl = gl0;
             e = e0;
-#pragma unroll 1
-            for (int j = 0; j < len; ++j)
-                if (step_fast(F, g1h, g1l, w1h, w1l)) return true;
-            return false;
+            return true;
         }
         n += len;
         return false;
@@ -466,9 +465,14 @@ struct Lane32 {
     }
 };
 
-// Terminal records waiting for the binary64 refinement, per warp, field-major.
-enum { B_G0H, B_G0L, B_G1H, B_G1L, B_W0H, B_W0L, B_W1H, B_W1L, B_NF };
-enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N1, B_ONSET, B_NI };
+// Records of ended rollouts waiting for the warp's flush, per warp,
+// field-major.  A window record (len > 0) holds the state at the start of the
+// window that contained the end and the lane's step constants; a terminal
+// record (len = 0, from a slow step) holds the last step's start and end pairs
+// (end pairs in the B_K .. B_NP3 slots) and its status.
+enum { B_VH, B_VL, B_GH, B_GL, B_E, B_K, B_NP1, B_NP2, B_NP3, B_NP4, B_NMP, B_SP, B_C, B_NF };
+enum { B_G1H = B_K, B_G1L = B_NP1, B_W1H = B_NP2, B_W1L = B_NP3 };
+enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
 constexpr int kColdWords = L_NW * 32;
 __host__ __device__ constexpr int warp_words(int T)
@@ -477,11 +481,13 @@ __host__ __device__ constexpr int warp_words(int T)
 }
 __host__ __device__ constexpr size_t smem_per_block(int T) { return sizeof(float) * warp_words(T) * kWarps; }
 
-// Binary64 refinement of the last step for the warp's queued records, all 32
-// lanes at once (Sec. V-D termination; the refinement of the last step).
-__device__ __forceinline__ void flush_batch(const ModelDev &M, const ParamsDev &P,
-                                            const OutDev &O, const float *bf, const int *bi,
-                                            int count)
+// For the warp's queued records, all 32 lanes at once: replay the windows that
+// contained an end one checked step at a time, then the binary64 refinement
+// of the last step (Sec. V-D termination; the refinement of the last step).
+template <bool LEAD, bool TTC>
+__device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F,
+                                            const ParamsDev &P, const OutDev &O,
+                                            const float *bf, const int *bi, int count)
 {
     __syncwarp();
     const int j = threadIdx.x & 31;
@@ -490,14 +496,53 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ParamsDev &
                            ((uint64_t)(uint32_t)bi[B_IDXHI * 32 + j] << 32);
         const uint64_t pi = (uint64_t)(uint32_t)bi[B_PIDXLO * 32 + j] |
                             ((uint64_t)(uint32_t)bi[B_PIDXHI * 32 + j] << 32);
-        const int status = bi[B_STATUS * 32 + j];
-        const int32_t n1 = bi[B_N1 * 32 + j];
+        const int len = bi[B_LEN * 32 + j];
         const int32_t on = bi[B_ONSET * 32 + j];
+        int status;
+        int32_t n1;
+        float g0h, g0l, w0h, w0l, g1h, g1l, w1h, w1l;
+        if (len > 0) {
+            Lane32<LEAD, TTC> R;
+            R.vh = bf[B_VH * 32 + j];
+            R.vl = bf[B_VL * 32 + j];
+            R.gh = bf[B_GH * 32 + j];
+            R.gl = bf[B_GL * 32 + j];
+            R.e = bf[B_E * 32 + j];
+            R.k = bf[B_K * 32 + j];
+            R.np1 = bf[B_NP1 * 32 + j];
+            R.np2 = bf[B_NP2 * 32 + j];
+            R.np3 = bf[B_NP3 * 32 + j];
+            R.np4 = bf[B_NP4 * 32 + j];
+            R.nmP = bf[B_NMP * 32 + j];
+            R.sp = bf[B_SP * 32 + j];
+            R.C = bf[B_C * 32 + j];
+            R.n = bi[B_N * 32 + j];
+            // ends within len steps: the window's last state is terminal
+            for (int s = 1; !R.step_fast(F, g1h, g1l, w1h, w1l) && s < len; ++s) {
+            }
+            g0h = R.gh;
+            g0l = R.gl;
+            w0h = R.vh;
+            w0l = R.vl;
+            n1 = R.n + 1;
+            status = (LEAD && g1h <= 0.0f) ? AEB_CONTACT : AEB_STOP;
+        } else {
+            g0h = bf[B_GH * 32 + j];
+            g0l = bf[B_GL * 32 + j];
+            w0h = bf[B_VH * 32 + j];
+            w0l = bf[B_VL * 32 + j];
+            g1h = bf[B_G1H * 32 + j];
+            g1l = bf[B_G1L * 32 + j];
+            w1h = bf[B_W1H * 32 + j];
+            w1l = bf[B_W1L * 32 + j];
+            n1 = bi[B_N * 32 + j];
+            status = bi[B_STATUS * 32 + j];
+        }
         const double d0 = __ldg(P.col[kD0] + pi);
-        const double x0 = d0 - ((double)bf[B_G0H * 32 + j] + (double)bf[B_G0L * 32 + j]);
-        const double x1 = d0 - ((double)bf[B_G1H * 32 + j] + (double)bf[B_G1L * 32 + j]);
-        const double w0 = (double)bf[B_W0H * 32 + j] + (double)bf[B_W0L * 32 + j];
-        const double w1 = (double)bf[B_W1H * 32 + j] + (double)bf[B_W1L * 32 + j];
+        const double x0 = d0 - ((double)g0h + (double)g0l);
+        const double x1 = d0 - ((double)g1h + (double)g1l);
+        const double w0 = (double)w0h + (double)w0l;
+        const double w1 = (double)w1h + (double)w1l;
         const double n = (double)(n1 - 1);
         if (status == AEB_CONTACT) {
             const double s = (d0 - x0) / (x1 - x0);
@@ -570,7 +615,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 need = (need & ~taken) | __ballot_sync(kFull, ended);
             }
             if (!__any_sync(kFull, active)) {
-                flush_batch(M, P, O, bf, bi, bcount);
+                flush_batch<LEAD, TTC>(M, F, P, O, bf, bi, bcount);
                 return;
             }
         }
@@ -589,38 +634,54 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         }
         const bool win = active && !slow;
         const int len = win ? L.window_len() : AEB_FP32_WINDOW;
+        bool replay = false;
         if (__all_sync(kFull, len == AEB_FP32_WINDOW)) {
-            if (win) ended = L.template step_window<true>(F, len, g1h, g1l, w1h, w1l);
+            if (win) replay = L.template step_window<true>(F, len);
         } else {
-            if (win) ended = L.template step_window<false>(F, len, g1h, g1l, w1h, w1l);
+            if (win) replay = L.template step_window<false>(F, len);
         }
+        ended = ended || replay;
         const unsigned endm = __ballot_sync(kFull, ended);
         if (endm) {
             const int cnt = __popc(endm);
             if (bcount + cnt > 32) {
-                flush_batch(M, P, O, bf, bi, bcount);
+                flush_batch<LEAD, TTC>(M, F, P, O, bf, bi, bcount);
                 bcount = 0;
             }
             if (ended) {
-                const int status = (LEAD && g1h <= 0.0f)
-                                       ? AEB_CONTACT
-                                       : (w1h <= 0.0f ? AEB_STOP : AEB_HORIZON);
                 const int j = bcount + __popc(endm & lanemask_lt());
-                bf[B_G0H * 32 + j] = L.gh;
-                bf[B_G0L * 32 + j] = L.gl;
-                bf[B_G1H * 32 + j] = g1h;
-                bf[B_G1L * 32 + j] = g1l;
-                bf[B_W0H * 32 + j] = L.vh;
-                bf[B_W0L * 32 + j] = L.vl;
-                bf[B_W1H * 32 + j] = w1h;
-                bf[B_W1L * 32 + j] = w1l;
+                bf[B_VH * 32 + j] = L.vh;
+                bf[B_VL * 32 + j] = L.vl;
+                bf[B_GH * 32 + j] = L.gh;
+                bf[B_GL * 32 + j] = L.gl;
                 bi[B_IDXLO * 32 + j] = (int)(uint32_t)idx;
                 bi[B_IDXHI * 32 + j] = (int)(uint32_t)(idx >> 32);
                 bi[B_PIDXLO * 32 + j] = L.ci(L_PIDXLO);
                 bi[B_PIDXHI * 32 + j] = L.ci(L_PIDXHI);
-                bi[B_STATUS * 32 + j] = status;
-                bi[B_N1 * 32 + j] = L.n + 1;
                 bi[B_ONSET * 32 + j] = L.onset();
+                if (replay) {
+                    bf[B_E * 32 + j] = L.e;
+                    bf[B_K * 32 + j] = L.k;
+                    bf[B_NP1 * 32 + j] = L.np1;
+                    bf[B_NP2 * 32 + j] = L.np2;
+                    bf[B_NP3 * 32 + j] = L.np3;
+                    bf[B_NP4 * 32 + j] = L.np4;
+                    bf[B_NMP * 32 + j] = L.nmP;
+                    bf[B_SP * 32 + j] = L.sp;
+                    bf[B_C * 32 + j] = L.C;
+                    bi[B_N * 32 + j] = L.n;
+                    bi[B_LEN * 32 + j] = len;
+                } else {
+                    bf[B_G1H * 32 + j] = g1h;
+                    bf[B_G1L * 32 + j] = g1l;
+                    bf[B_W1H * 32 + j] = w1h;
+                    bf[B_W1L * 32 + j] = w1l;
+                    bi[B_STATUS * 32 + j] = (LEAD && g1h <= 0.0f)
+                                                ? AEB_CONTACT
+                                                : (w1h <= 0.0f ? AEB_STOP : AEB_HORIZON);
+                    bi[B_N * 32 + j] = L.n + 1;
+                    bi[B_LEN * 32 + j] = 0;
+                }
             }
             bcount += cnt;
             need = endm;
