@@ -1,7 +1,14 @@
 // rollout_fp32.cu -- binary32 rollout kernel with compensated state.
 //
 // The RK4 stages of Eq. 7-9 (Sec. IV-D) run in binary32 with fused
-// multiply-add.  Speed and the gap to the lead (g = d0 - x) are carried as
+// multiply-add, in scaled units: the lane carries w = s v with s = sqrt(k)
+// (k = rho C_d A / (2 m)), so the drag term k v^2 of a stage is w^2 and a
+// stage costs one FMA for drag plus one for the actuator term, and the gap
+// G = sigma (d0 - x) with sigma = s / h6 (h6 the binary32 step factor of the
+// speed update), so the position increment of a step is the plain weighted
+// sum of the stage speeds, with no multiply.  (s is rounded to binary32, so
+// the drag coefficient in effect is s^2, within 2e-7 relative of k.)
+// Speed and gap are carried as
 // unevaluated double-float pairs (hi + lo): each step's increment is added with
 // Fast2Sum and its rounding error kept in lo, so 1e4-1e5 increments of
 // 1e-3-1e-4 relative size do not lose the ~1e-7 relative precision of a
@@ -31,10 +38,11 @@
 // stages, then moves to the next piece.
 //
 // Binary64 runs at 1/64 of the binary32 rate on GB300, so it is kept out of the
-// step loop and done at full SIMT width: when a warp claims a tile of 64
+// step loop and done at full SIMT width: when a warp claims a tile of
 // samples, all 32 lanes prepare the tile's binary32 constants together into
-// shared memory (brake-onset step by the binary64 rule, hi/lo splits of v0 and
-// d0, drag and cap coefficients, actuator multipliers).  Lanes whose rollout
+// shared memory (brake-onset step by the binary64 rule, hi/lo splits of the
+// scaled v0 and d0, scaled step factors, cap coefficients, actuator
+// multipliers, the scaled TTC threshold and range noise).  Lanes whose rollout
 // ends refill from that tile.  The binary64 refinement of the last step (linear
 // stop/contact interpolation from the hi + lo pairs) is also batched: an ending
 // lane queues its terminal state in the warp's shared slab, and the warp refines
@@ -67,22 +75,24 @@ constexpr int kThreads = 32 * kWarps;
 
 // prepared per-sample record, stored field-major in shared memory
 enum {
-    R_V0H, R_V0L, R_D0H, R_D0L, R_GS, R_K, R_F0, R_F1, R_R0, R_R1, R_MG,
-    R_NP1, R_NP2, R_NP3, R_NP4, R_P4, R_NMP, R_NZ, R_NF  // float fields
+    R_W0H, R_W0L, R_G0H, R_G0L, R_GS, R_S, R_NH2S, R_NDTS, R_NH6S, R_F0, R_F1, R_R0,
+    R_R1, R_MG, R_NP1, R_NP2, R_NP3, R_NP4, R_P4, R_NMP, R_NZ, R_THRH, R_THRL,
+    R_NF  // float fields
 };
 enum { R_NDELAY, R_KIND, R_NI };  // int fields
 enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 
 struct ModelF32 {
-    float dt, h6, nh2, nh6, ndt, acmd;
+    float acmd;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 
-// Prepare samples [start, start + cnt) of a tile into the warp's shared slab.
+// Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
+// warp's shared slab.
 template <bool LEAD, bool TTC>
 __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P, uint64_t start,
-                                          int cnt, int T, float *tf, int *ti)
+                                          int cnt, double thr, int T, float *tf, int *ti)
 {
     for (int j = threadIdx.x & 31; j < cnt; j += 32) {
         const uint64_t i = start + j;
@@ -100,14 +110,24 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         ti[R_NDELAY * T + j] = nd;
         ti[R_KIND * T + j] = kind;
         if (kind != K_RUN) continue;
-        const float v0h = __double2float_rn(f[kV0]);
-        const float d0h = __double2float_rn(f[kD0]);
-        tf[R_V0H * T + j] = v0h;
-        tf[R_V0L * T + j] = __double2float_rn(f[kV0] - (double)v0h);
-        tf[R_D0H * T + j] = d0h;
-        tf[R_D0L * T + j] = __double2float_rn(f[kD0] - (double)d0h);
+        // speed scale s = sqrt(k), bounded below so that a drag-free sample
+        // keeps its scaled state in the normal binary32 range
+        const float k32 = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
+        const float sc = fmaxf(sqrtf(k32), 1e-18f);
+        const double sd = (double)sc;
+        const float nh6s = __double2float_rn(-(sd * M.h6));
+        const double sigma = (sd * sd) / -(double)nh6s;  // gap scale s / h6
+        const double w0 = sd * f[kV0], g0 = sigma * f[kD0];
+        const float w0h = __double2float_rn(w0), g0h = __double2float_rn(g0);
+        tf[R_W0H * T + j] = w0h;
+        tf[R_W0L * T + j] = __double2float_rn(w0 - (double)w0h);
+        tf[R_G0H * T + j] = g0h;
+        tf[R_G0L * T + j] = __double2float_rn(g0 - (double)g0h);
         tf[R_GS * T + j] = __double2float_rn(f[kGs]);
-        tf[R_K * T + j] = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
+        tf[R_S * T + j] = sc;
+        tf[R_NH2S * T + j] = __double2float_rn(-(sd * M.h2));
+        tf[R_NDTS * T + j] = __double2float_rn(-(sd * M.dt));
+        tf[R_NH6S * T + j] = nh6s;
         const double mu = f[kMu], mh = mu * M.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
             tf[R_F0 * T + j] = finf();
@@ -141,7 +161,13 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
             tf[R_P4 * T + j] = 0.0f;
             tf[R_NMP * T + j] = -1.0f;
         }
-        tf[R_NZ * T + j] = TTC ? __double2float_rn(f[kNoise]) : 0.0f;
+        if (TTC) {  // (g + noise) - thr v scaled by sigma: G + sigma noise - (sigma thr / s) w
+            const double ts = thr * (sigma / sd);
+            const float tsh = __double2float_rn(ts);
+            tf[R_NZ * T + j] = __double2float_rn(sigma * f[kNoise]);
+            tf[R_THRH * T + j] = tsh;
+            tf[R_THRL * T + j] = __double2float_rn(ts - (double)tsh);
+        }
     }
 }
 
@@ -149,16 +175,18 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 // test, records) live in a column of the warp's shared slab, field-major with
 // stride 32, to keep the step loop's register budget small.
 enum {
-    L_F0, L_F1, L_R0, L_R1, L_MG, L_P4, L_GS, L_U, L_NZ, L_THRH, L_THRL,  // floats
-    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI,                                   // ints
+    L_F0, L_F1, L_R0, L_R1, L_MG, L_P4, L_GS, L_U, L_NZ, L_THRH, L_THRL, L_S, L_ETHK,  // floats
+    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                 // ints
     L_NW
 };
 
 template <bool LEAD, bool TTC>
 struct Lane32 {
-    float vh, vl, gh, gl, e;      // state: speed, gap d0 - x, actuator deviation a - u
-    float C, sp, eth, ethK;       // current piece of r(D), window threshold
-    float k, np1, np2, np3, np4, nmP;
+    float vh, vl, gh, gl, e;      // state: scaled speed w = s v, scaled gap G = sigma (d0 - x),
+                                  // actuator deviation a - u
+    float C, sp, eth;             // current piece of r(D), its threshold on e
+    float nh2s, ndts, nh6s;       // scaled step factors -s dt/2, -s dt, -s dt/6
+    float np1, np2, np3, np4, nmP;
     int32_t n, ev;                // step, next slow step
     bool trig;
     float *cold;                  // this lane's column: cold[field * 32]
@@ -200,13 +228,14 @@ struct Lane32 {
         eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
         // e decays by (1 - mP) per step; a window of K steps stays inside the
         // piece if its last step does: e (1 - mP)^(K-1) >= eth (with margin)
-        ethK = eth;
+        float ethK = eth;
         if (eth > 0.0f) {
             float f = 1.0f;
 #pragma unroll
             for (int j = 1; j < AEB_FP32_WINDOW; ++j) f *= (1.0f + nmP);
             ethK = (f > 0.0f) ? (eth / f) * 1.000001f : finf();
         }
+        set_cf(L_ETHK, ethK);
     }
 
     // r + g sin(theta) by the full minimum (slow steps)
@@ -233,17 +262,19 @@ struct Lane32 {
 
     // Common tail of a step: position / speed increments, compensated updates,
     // actuator decay.  Returns the end-of-step pairs in the out-parameters.
-    __device__ __forceinline__ void advance(const ModelF32 &F, float q1, float q2, float q3,
-                                            float q4, float v2, float v3, float v4, float &g1h,
-                                            float &g1l, float &w1h, float &w1l, float &en) const
+    __device__ __forceinline__ void advance(float q1, float q2, float q3, float q4, float v2,
+                                            float v3, float v4, float &g1h, float &g1l,
+                                            float &w1h, float &w1l, float &en) const
     {
-        // Both increments carry the same binary32 step factor h6 = dt/6: a
-        // position increment formed with dt instead would scale distance
-        // against speed by the ratio of two independently rounded constants
-        // (a systematic ~5e-8 relative error in every stopping distance).
-        const float dx = fmaf(F.dt, vl, F.h6 * fmaf(2.0f, v2 + v3, vh + v4));
+        // The gap scale sigma = s / h6 is built from the same binary32 speed
+        // factor nh6s = -s h6, so distance and speed advance with one step
+        // factor (independently rounded factors would scale every stopping
+        // distance by their ratio, a systematic ~5e-8 relative error).  The
+        // stage speeds are formed from the high word, so lo enters with the
+        // full weight 1 + 2 + 2 + 1 = 6.
+        const float dx = fmaf(6.0f, vl, fmaf(2.0f, v2 + v3, vh + v4));
         // Fast2Sum of (hi, lo + increment) keeps each pair normalised
-        const float tv = fmaf(F.nh6, fmaf(2.0f, q2 + q3, q1 + q4), vl);
+        const float tv = fmaf(nh6s, fmaf(2.0f, q2 + q3, q1 + q4), vl);
         w1h = vh + tv;
         w1l = tv - (w1h - vh);
         const float tg = gl - dx;
@@ -268,15 +299,15 @@ struct Lane32 {
                                               float &w1h, float &w1l)
     {
         const float S = sp * e;
-        const float q1 = fmaf(k * vh, vh, fmaf(S, np1, C));
-        const float v2 = fmaf(F.nh2, q1, vh);
-        const float q2 = fmaf(k * v2, v2, fmaf(S, np2, C));
-        const float v3 = fmaf(F.nh2, q2, vh);
-        const float q3 = fmaf(k * v3, v3, fmaf(S, np3, C));
-        const float v4 = fmaf(F.ndt, q3, vh);
-        const float q4 = fmaf(k * v4, v4, fmaf(S, np4, C));
+        const float q1 = fmaf(vh, vh, fmaf(S, np1, C));
+        const float v2 = fmaf(nh2s, q1, vh);
+        const float q2 = fmaf(v2, v2, fmaf(S, np2, C));
+        const float v3 = fmaf(nh2s, q2, vh);
+        const float q3 = fmaf(v3, v3, fmaf(S, np3, C));
+        const float v4 = fmaf(ndts, q3, vh);
+        const float q4 = fmaf(v4, v4, fmaf(S, np4, C));
         float en;
-        advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
+        advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f;
         if (!ended) commit(g1h, g1l, w1h, w1l, en);
         return ended;
@@ -292,7 +323,7 @@ struct Lane32 {
         if (TTC && !trig) return 1;
         const int32_t room = ev - n;  // >= 1: a lane at its event takes the slow path
         int len = room < AEB_FP32_WINDOW ? (int)room : AEB_FP32_WINDOW;
-        if (e < ethK) {  // close to a breakpoint (eth > 0 here)
+        if (e < cf(L_ETHK)) {  // close to a breakpoint (eth > 0 here)
             const float q = 1.0f + nmP, m = eth * 1.000001f;
             int lb = 1;
             if (q > 0.0f && q < 1.0f) lb = (e * (q * q * q) >= m) ? 4 : ((e * q >= m) ? 2 : 1);
@@ -322,15 +353,15 @@ struct Lane32 {
         for (int j = 0; j < AEB_FP32_WINDOW; ++j) {
             if (!FULL && j >= len) break;
             const float S = sp * e;
-            const float q1 = fmaf(k * vh, vh, fmaf(S, np1, C));
-            const float v2 = fmaf(F.nh2, q1, vh);
-            const float q2 = fmaf(k * v2, v2, fmaf(S, np2, C));
-            const float v3 = fmaf(F.nh2, q2, vh);
-            const float q3 = fmaf(k * v3, v3, fmaf(S, np3, C));
-            const float v4 = fmaf(F.ndt, q3, vh);
-            const float q4 = fmaf(k * v4, v4, fmaf(S, np4, C));
+            const float q1 = fmaf(vh, vh, fmaf(S, np1, C));
+            const float v2 = fmaf(nh2s, q1, vh);
+            const float q2 = fmaf(v2, v2, fmaf(S, np2, C));
+            const float v3 = fmaf(nh2s, q2, vh);
+            const float q3 = fmaf(v3, v3, fmaf(S, np3, C));
+            const float v4 = fmaf(ndts, q3, vh);
+            const float q4 = fmaf(v4, v4, fmaf(S, np4, C));
             float en;
-            advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
+            advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
             vh = w1h;
             vl = w1l;
             gh = g1h;
@@ -370,15 +401,15 @@ struct Lane32 {
             set_cf(L_U, F.acmd);
             e = e - F.acmd;
         }
-        const float q1 = fmaf(k * vh, vh, rg_full(np1));
-        const float v2 = fmaf(F.nh2, q1, vh);
-        const float q2 = fmaf(k * v2, v2, rg_full(np2));
-        const float v3 = fmaf(F.nh2, q2, vh);
-        const float q3 = fmaf(k * v3, v3, rg_full(np3));
-        const float v4 = fmaf(F.ndt, q3, vh);
-        const float q4 = fmaf(k * v4, v4, rg_full(np4));
+        const float q1 = fmaf(vh, vh, rg_full(np1));
+        const float v2 = fmaf(nh2s, q1, vh);
+        const float q2 = fmaf(v2, v2, rg_full(np2));
+        const float v3 = fmaf(nh2s, q2, vh);
+        const float q3 = fmaf(v3, v3, rg_full(np3));
+        const float v4 = fmaf(ndts, q3, vh);
+        const float q4 = fmaf(v4, v4, rg_full(np4));
         float en;
-        advance(F, q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
+        advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
         if (!ended) {
             commit(g1h, g1l, w1h, w1l, en);
@@ -406,10 +437,10 @@ struct Lane32 {
         }
     }
 
-    // Load sample `slot` of the warp's tile (parameter row pi, output row i, TTC
-    // threshold thr); true if it ended at once (stored).
+    // Load sample `slot` of the warp's tile (parameter row pi, output row i);
+    // true if it ended at once (stored).
     __device__ __forceinline__ bool init(const ModelDev &M, const ParamsDev &P, const OutDev &O,
-                                         uint64_t pi, uint64_t i, double thr, int slot, int T,
+                                         uint64_t pi, uint64_t i, int slot, int T,
                                          const float *tf, const int *ti)
     {
         const int kind = ti[R_KIND * T + slot];
@@ -428,11 +459,13 @@ struct Lane32 {
             }
             return true;
         }
-        vh = tf[R_V0H * T + slot];
-        vl = tf[R_V0L * T + slot];
-        gh = tf[R_D0H * T + slot];
-        gl = tf[R_D0L * T + slot];
-        k = tf[R_K * T + slot];
+        vh = tf[R_W0H * T + slot];
+        vl = tf[R_W0L * T + slot];
+        gh = tf[R_G0H * T + slot];
+        gl = tf[R_G0L * T + slot];
+        nh2s = tf[R_NH2S * T + slot];
+        ndts = tf[R_NDTS * T + slot];
+        nh6s = tf[R_NH6S * T + slot];
         np1 = tf[R_NP1 * T + slot];
         np2 = tf[R_NP2 * T + slot];
         np3 = tf[R_NP3 * T + slot];
@@ -445,14 +478,16 @@ struct Lane32 {
         set_cf(L_R1, tf[R_R1 * T + slot]);
         set_cf(L_MG, tf[R_MG * T + slot]);
         set_cf(L_P4, tf[R_P4 * T + slot]);
+        set_cf(L_S, tf[R_S * T + slot]);
         set_ci(L_NDELAY, n_delay);
         set_ci(L_PIDXLO, (int)(uint32_t)pi);
         set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
+        set_ci(L_IDXLO, (int)(uint32_t)i);
+        set_ci(L_IDXHI, (int)(uint32_t)(i >> 32));
         if (TTC) {
-            const float thr_h = __double2float_rn(thr);
             set_cf(L_NZ, tf[R_NZ * T + slot]);
-            set_cf(L_THRH, thr_h);
-            set_cf(L_THRL, __double2float_rn(thr - (double)thr_h));
+            set_cf(L_THRH, tf[R_THRH * T + slot]);
+            set_cf(L_THRL, tf[R_THRL * T + slot]);
         }
         e = 0.0f;  // a = 0 and the command is 0 before onset
         set_cf(L_U, 0.0f);
@@ -469,9 +504,13 @@ struct Lane32 {
 // field-major.  A window record (len > 0) holds the state at the start of the
 // window that contained the end and the lane's step constants; a terminal
 // record (len = 0, from a slow step) holds the last step's start and end pairs
-// (end pairs in the B_K .. B_NP3 slots) and its status.
-enum { B_VH, B_VL, B_GH, B_GL, B_E, B_K, B_NP1, B_NP2, B_NP3, B_NP4, B_NMP, B_SP, B_C, B_NF };
-enum { B_G1H = B_K, B_G1L = B_NP1, B_W1H = B_NP2, B_W1L = B_NP3 };
+// (end pairs in the B_NP1 .. B_NP4 slots) and its status.  Both keep the
+// scales s (B_S) and -s h6 (B_NH6S) that undo the scaled units.
+enum {
+    B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NDTS, B_NH6S, B_NP1, B_NP2, B_NP3, B_NP4, B_NMP,
+    B_SP, B_C, B_S, B_NF
+};
+enum { B_G1H = B_NP1, B_G1L = B_NP2, B_W1H = B_NP3, B_W1L = B_NP4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
 constexpr int kColdWords = L_NW * 32;
@@ -508,7 +547,9 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.gh = bf[B_GH * 32 + j];
             R.gl = bf[B_GL * 32 + j];
             R.e = bf[B_E * 32 + j];
-            R.k = bf[B_K * 32 + j];
+            R.nh2s = bf[B_NH2S * 32 + j];
+            R.ndts = bf[B_NDTS * 32 + j];
+            R.nh6s = bf[B_NH6S * 32 + j];
             R.np1 = bf[B_NP1 * 32 + j];
             R.np2 = bf[B_NP2 * 32 + j];
             R.np3 = bf[B_NP3 * 32 + j];
@@ -539,10 +580,12 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             status = bi[B_STATUS * 32 + j];
         }
         const double d0 = __ldg(P.col[kD0] + pi);
-        const double x0 = d0 - ((double)g0h + (double)g0l);
-        const double x1 = d0 - ((double)g1h + (double)g1l);
-        const double w0 = (double)w0h + (double)w0l;
-        const double w1 = (double)w1h + (double)w1l;
+        const double sd = (double)bf[B_S * 32 + j];
+        const double sigma = (sd * sd) / -(double)bf[B_NH6S * 32 + j];
+        const double x0 = d0 - ((double)g0h + (double)g0l) / sigma;
+        const double x1 = d0 - ((double)g1h + (double)g1l) / sigma;
+        const double w0 = ((double)w0h + (double)w0l) / sd;
+        const double w1 = ((double)w1h + (double)w1l) / sd;
         const double n = (double)(n1 - 1);
         if (status == AEB_CONTACT) {
             const double s = (d0 - x0) / (x1 - x0);
@@ -579,7 +622,6 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     bool dry = false;
     Lane32<LEAD, TTC> L;
     L.cold = coldw + lane;
-    uint64_t idx = 0;
     bool active = false;
     unsigned need = kFull;
     for (;;) {
@@ -598,7 +640,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     tile = nt;
                     cursor = 0;
                     __syncwarp();  // every lane has read its record of the previous tile
-                    prep_tile<LEAD, TTC>(M, P, tile.p0, tile.count, T, tf, ti);
+                    prep_tile<LEAD, TTC>(M, P, tile.p0, tile.count, tile.thr, T, tf, ti);
                     __syncwarp();
                 }
                 const unsigned rank = __popc(need & lanemask_lt());
@@ -606,9 +648,8 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 bool ended = false;
                 if (got) {
                     const int slot = cursor + (int)rank;
-                    idx = tile.o0 + slot;
                     active = true;
-                    ended = L.init(M, P, O, tile.p0 + slot, idx, tile.thr, slot, T, tf, ti);
+                    ended = L.init(M, P, O, tile.p0 + slot, tile.o0 + slot, slot, T, tf, ti);
                 }
                 const unsigned taken = __ballot_sync(kFull, got);
                 cursor += __popc(taken);
@@ -654,14 +695,17 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 bf[B_VL * 32 + j] = L.vl;
                 bf[B_GH * 32 + j] = L.gh;
                 bf[B_GL * 32 + j] = L.gl;
-                bi[B_IDXLO * 32 + j] = (int)(uint32_t)idx;
-                bi[B_IDXHI * 32 + j] = (int)(uint32_t)(idx >> 32);
+                bf[B_NH6S * 32 + j] = L.nh6s;
+                bf[B_S * 32 + j] = L.cf(L_S);
+                bi[B_IDXLO * 32 + j] = L.ci(L_IDXLO);
+                bi[B_IDXHI * 32 + j] = L.ci(L_IDXHI);
                 bi[B_PIDXLO * 32 + j] = L.ci(L_PIDXLO);
                 bi[B_PIDXHI * 32 + j] = L.ci(L_PIDXHI);
                 bi[B_ONSET * 32 + j] = L.onset();
                 if (replay) {
                     bf[B_E * 32 + j] = L.e;
-                    bf[B_K * 32 + j] = L.k;
+                    bf[B_NH2S * 32 + j] = L.nh2s;
+                    bf[B_NDTS * 32 + j] = L.ndts;
                     bf[B_NP1 * 32 + j] = L.np1;
                     bf[B_NP2 * 32 + j] = L.np2;
                     bf[B_NP3 * 32 + j] = L.np3;
@@ -692,11 +736,6 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
 ModelF32 to_f32(const ModelDev &m)
 {
     ModelF32 f;
-    f.dt = (float)m.dt;
-    f.h6 = (float)m.h6;
-    f.nh2 = -(float)m.h2;
-    f.nh6 = -(float)m.h6;
-    f.ndt = -(float)m.dt;
     f.acmd = (float)m.a_cmd;
     return f;
 }
