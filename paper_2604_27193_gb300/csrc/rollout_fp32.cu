@@ -33,7 +33,8 @@
 // lane keeps the line that is the minimum at the step's smallest demand and the
 // threshold on e beyond which the step's largest demand would pass the next
 // breakpoint.  Inside a piece every stage costs one FMA:
-//     r_j + g sin(theta) = C - (slope e) p_j,  C = intercept - slope u + g sin(theta).
+//     r_j + g sin(theta) = C + e a_j,  a_j = -slope p_j,
+//     C = intercept - slope u + g sin(theta).
 // A step that crosses a breakpoint evaluates the full minimum for its four
 // stages, then moves to the next piece.
 //
@@ -48,7 +49,7 @@
 // lane queues its terminal state in the warp's shared slab, and the warp refines
 // 32 queued rollouts at once.
 //
-// Steps run in windows of up to K = 8 with no test in between.  A lane's
+// Steps run in windows of up to K = 16 with no test in between.  A lane's
 // window ends before its next event (brake onset, the last step before the
 // horizon, a step that crosses a breakpoint of r(D)); lanes of a warp with
 // shorter windows run the same window code masked, so a lane close to an event
@@ -67,7 +68,7 @@ constexpr int kTileMax = 256;
 constexpr int kWarps = 4;      // warps per block
 constexpr int kThreads = 32 * kWarps;
 #ifndef AEB_FP32_WINDOW
-#define AEB_FP32_WINDOW 8      // steps a lane runs without termination tests
+#define AEB_FP32_WINDOW 16     // steps a lane runs without termination tests
 #endif
 #ifndef AEB_FP32_MIN_BLOCKS
 #define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
@@ -176,6 +177,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 // stride 32, to keep the step loop's register budget small.
 enum {
     L_F0, L_F1, L_R0, L_R1, L_MG, L_P4, L_GS, L_U, L_NZ, L_THRH, L_THRL, L_S, L_ETHK,  // floats
+    L_NP1, L_NP2, L_NP3, L_NP4,
     L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                 // ints
     L_NW
 };
@@ -184,9 +186,10 @@ template <bool LEAD, bool TTC>
 struct Lane32 {
     float vh, vl, gh, gl, e;      // state: scaled speed w = s v, scaled gap G = sigma (d0 - x),
                                   // actuator deviation a - u
-    float C, sp, eth;             // current piece of r(D), its threshold on e
+    float C, eth;                 // current piece of r(D), its threshold on e
     float nh2s, ndts, nh6s;       // scaled step factors -s dt/2, -s dt, -s dt/6
-    float np1, np2, np3, np4, nmP;
+    float a1, a2, a3, a4;         // slope of the piece times -p_j
+    float nmP;
     int32_t n, ev;                // step, next slow step
     bool trig;
     float *cold;                  // this lane's column: cold[field * 32]
@@ -223,7 +226,10 @@ struct Lane32 {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (b_[j] < bb) B = fminf(B, (a_[j] - ab) / (bb - b_[j]));
-        sp = bb;
+        a1 = bb * cf(L_NP1);
+        a2 = bb * cf(L_NP2);
+        a3 = bb * cf(L_NP3);
+        a4 = bb * cf(L_NP4);
         C = (ab - bb * u) + cf(L_GS);
         eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
         // e decays by (1 - mP) per step; a window of K steps stays inside the
@@ -293,24 +299,42 @@ struct Lane32 {
         n = n + 1;
     }
 
-    // A step inside the current piece of r(D): one FMA per stage for r.
-    // Returns true if the rollout ended (contact or stop) in this step.
-    __device__ __forceinline__ bool step_fast(const ModelF32 &F, float &g1h, float &g1l,
-                                              float &w1h, float &w1l)
+    // The end-of-step pairs and actuator deviation of a step inside the
+    // current piece of r(D): one FMA per stage for r.
+    __device__ __forceinline__ void piece_step(float &g1h, float &g1l, float &w1h, float &w1l,
+                                               float &en) const
     {
-        const float S = sp * e;
-        const float q1 = fmaf(vh, vh, fmaf(S, np1, C));
+        const float q1 = fmaf(vh, vh, fmaf(e, a1, C));
         const float v2 = fmaf(nh2s, q1, vh);
-        const float q2 = fmaf(v2, v2, fmaf(S, np2, C));
+        const float q2 = fmaf(v2, v2, fmaf(e, a2, C));
         const float v3 = fmaf(nh2s, q2, vh);
-        const float q3 = fmaf(v3, v3, fmaf(S, np3, C));
+        const float q3 = fmaf(v3, v3, fmaf(e, a3, C));
         const float v4 = fmaf(ndts, q3, vh);
-        const float q4 = fmaf(v4, v4, fmaf(S, np4, C));
-        float en;
+        const float q4 = fmaf(v4, v4, fmaf(e, a4, C));
         advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
+    }
+
+    // A checked step inside the current piece; true if the rollout ended
+    // (contact or stop) in this step, which is then not committed.
+    __device__ __forceinline__ bool step_fast(float &g1h, float &g1l, float &w1h, float &w1l)
+    {
+        float en;
+        piece_step(g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f;
         if (!ended) commit(g1h, g1l, w1h, w1l, en);
         return ended;
+    }
+
+    // An unchecked step inside the current piece (step counter not advanced).
+    __device__ __forceinline__ void step_unchecked()
+    {
+        float g1h, g1l, w1h, w1l, en;
+        piece_step(g1h, g1l, w1h, w1l, en);
+        vh = w1h;
+        vl = w1l;
+        gh = g1h;
+        gl = g1l;
+        e = en;
     }
 
     // How many steps (1 .. K) may run as one window from here: none of them
@@ -326,7 +350,12 @@ struct Lane32 {
         if (e < cf(L_ETHK)) {  // close to a breakpoint (eth > 0 here)
             const float q = 1.0f + nmP, m = eth * 1.000001f;
             int lb = 1;
-            if (q > 0.0f && q < 1.0f) lb = (e * (q * q * q) >= m) ? 4 : ((e * q >= m) ? 2 : 1);
+            if (q > 0.0f && q < 1.0f) {
+                const float q2 = q * q, q3 = q2 * q;
+                lb = (e * q >= m) ? 2 : 1;
+                if (e * q3 >= m) lb = 4;
+                if (AEB_FP32_WINDOW > 8 && e * (q3 * q3 * q) >= m) lb = 8;
+            }
             len = len < lb ? len : lb;
         }
         return len;
@@ -342,31 +371,19 @@ struct Lane32 {
     // reproduces the same arithmetic (this file is compiled without FMA
     // contraction) and so finds the terminating step.  Lanes of a warp with
     // different lengths run the same window code, each masked off after its
-    // own length.
+    // own length (the short-window version is a rolled loop, to keep the
+    // kernel's code small).
     template <bool FULL>
-    __device__ __forceinline__ bool step_window(const ModelF32 &F, int len)
+    __device__ __forceinline__ bool step_window(int len)
     {
-        if (FULL) len = AEB_FP32_WINDOW;
-        float g1h, g1l, w1h, w1l;
         const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
+        if (FULL) {
+            len = AEB_FP32_WINDOW;
 #pragma unroll
-        for (int j = 0; j < AEB_FP32_WINDOW; ++j) {
-            if (!FULL && j >= len) break;
-            const float S = sp * e;
-            const float q1 = fmaf(vh, vh, fmaf(S, np1, C));
-            const float v2 = fmaf(nh2s, q1, vh);
-            const float q2 = fmaf(v2, v2, fmaf(S, np2, C));
-            const float v3 = fmaf(nh2s, q2, vh);
-            const float q3 = fmaf(v3, v3, fmaf(S, np3, C));
-            const float v4 = fmaf(ndts, q3, vh);
-            const float q4 = fmaf(v4, v4, fmaf(S, np4, C));
-            float en;
-            advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
-            vh = w1h;
-            vl = w1l;
-            gh = g1h;
-            gl = g1l;
-            e = en;
+            for (int j = 0; j < AEB_FP32_WINDOW; ++j) step_unchecked();
+        } else {
+#pragma unroll 1
+            for (int j = 0; j < len; ++j) step_unchecked();
         }
         if ((LEAD && gh <= 0.0f) || vh <= 0.0f) {
             vh = vh0;
@@ -387,7 +404,7 @@ struct Lane32 {
     {
         set_cf(L_U, F.acmd);
         e = e - F.acmd;
-        set_piece(-fmaf(-np1, e, F.acmd));
+        set_piece(-fmaf(-cf(L_NP1), e, F.acmd));
         ev = n_last;
     }
 
@@ -401,19 +418,19 @@ struct Lane32 {
             set_cf(L_U, F.acmd);
             e = e - F.acmd;
         }
-        const float q1 = fmaf(vh, vh, rg_full(np1));
+        const float q1 = fmaf(vh, vh, rg_full(cf(L_NP1)));
         const float v2 = fmaf(nh2s, q1, vh);
-        const float q2 = fmaf(v2, v2, rg_full(np2));
+        const float q2 = fmaf(v2, v2, rg_full(cf(L_NP2)));
         const float v3 = fmaf(nh2s, q2, vh);
-        const float q3 = fmaf(v3, v3, rg_full(np3));
+        const float q3 = fmaf(v3, v3, rg_full(cf(L_NP3)));
         const float v4 = fmaf(ndts, q3, vh);
-        const float q4 = fmaf(v4, v4, rg_full(np4));
+        const float q4 = fmaf(v4, v4, rg_full(cf(L_NP4)));
         float en;
         advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
         const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
         if (!ended) {
             commit(g1h, g1l, w1h, w1l, en);
-            set_piece(-fmaf(-np1, e, cf(L_U)));
+            set_piece(-fmaf(-cf(L_NP1), e, cf(L_U)));
             next_event(n_last);
         }
         return ended;
@@ -466,10 +483,10 @@ struct Lane32 {
         nh2s = tf[R_NH2S * T + slot];
         ndts = tf[R_NDTS * T + slot];
         nh6s = tf[R_NH6S * T + slot];
-        np1 = tf[R_NP1 * T + slot];
-        np2 = tf[R_NP2 * T + slot];
-        np3 = tf[R_NP3 * T + slot];
-        np4 = tf[R_NP4 * T + slot];
+        set_cf(L_NP1, tf[R_NP1 * T + slot]);
+        set_cf(L_NP2, tf[R_NP2 * T + slot]);
+        set_cf(L_NP3, tf[R_NP3 * T + slot]);
+        set_cf(L_NP4, tf[R_NP4 * T + slot]);
         nmP = tf[R_NMP * T + slot];
         set_cf(L_GS, tf[R_GS * T + slot]);
         set_cf(L_F0, tf[R_F0 * T + slot]);
@@ -504,13 +521,13 @@ struct Lane32 {
 // field-major.  A window record (len > 0) holds the state at the start of the
 // window that contained the end and the lane's step constants; a terminal
 // record (len = 0, from a slow step) holds the last step's start and end pairs
-// (end pairs in the B_NP1 .. B_NP4 slots) and its status.  Both keep the
+// (end pairs in the B_A1 .. B_A4 slots) and its status.  Both keep the
 // scales s (B_S) and -s h6 (B_NH6S) that undo the scaled units.
 enum {
-    B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NDTS, B_NH6S, B_NP1, B_NP2, B_NP3, B_NP4, B_NMP,
-    B_SP, B_C, B_S, B_NF
+    B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NDTS, B_NH6S, B_A1, B_A2, B_A3, B_A4, B_NMP,
+    B_C, B_S, B_NF
 };
-enum { B_G1H = B_NP1, B_G1L = B_NP2, B_W1H = B_NP3, B_W1L = B_NP4 };
+enum { B_G1H = B_A1, B_G1L = B_A2, B_W1H = B_A3, B_W1L = B_A4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
 constexpr int kColdWords = L_NW * 32;
@@ -550,16 +567,15 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.nh2s = bf[B_NH2S * 32 + j];
             R.ndts = bf[B_NDTS * 32 + j];
             R.nh6s = bf[B_NH6S * 32 + j];
-            R.np1 = bf[B_NP1 * 32 + j];
-            R.np2 = bf[B_NP2 * 32 + j];
-            R.np3 = bf[B_NP3 * 32 + j];
-            R.np4 = bf[B_NP4 * 32 + j];
+            R.a1 = bf[B_A1 * 32 + j];
+            R.a2 = bf[B_A2 * 32 + j];
+            R.a3 = bf[B_A3 * 32 + j];
+            R.a4 = bf[B_A4 * 32 + j];
             R.nmP = bf[B_NMP * 32 + j];
-            R.sp = bf[B_SP * 32 + j];
             R.C = bf[B_C * 32 + j];
             R.n = bi[B_N * 32 + j];
             // ends within len steps: the window's last state is terminal
-            for (int s = 1; !R.step_fast(F, g1h, g1l, w1h, w1l) && s < len; ++s) {
+            for (int s = 1; !R.step_fast(g1h, g1l, w1h, w1l) && s < len; ++s) {
             }
             g0h = R.gh;
             g0l = R.gl;
@@ -677,9 +693,9 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         const int len = win ? L.window_len() : AEB_FP32_WINDOW;
         bool replay = false;
         if (__all_sync(kFull, len == AEB_FP32_WINDOW)) {
-            if (win) replay = L.template step_window<true>(F, len);
+            if (win) replay = L.template step_window<true>(len);
         } else {
-            if (win) replay = L.template step_window<false>(F, len);
+            if (win) replay = L.template step_window<false>(len);
         }
         ended = ended || replay;
         const unsigned endm = __ballot_sync(kFull, ended);
@@ -706,12 +722,11 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     bf[B_E * 32 + j] = L.e;
                     bf[B_NH2S * 32 + j] = L.nh2s;
                     bf[B_NDTS * 32 + j] = L.ndts;
-                    bf[B_NP1 * 32 + j] = L.np1;
-                    bf[B_NP2 * 32 + j] = L.np2;
-                    bf[B_NP3 * 32 + j] = L.np3;
-                    bf[B_NP4 * 32 + j] = L.np4;
+                    bf[B_A1 * 32 + j] = L.a1;
+                    bf[B_A2 * 32 + j] = L.a2;
+                    bf[B_A3 * 32 + j] = L.a3;
+                    bf[B_A4 * 32 + j] = L.a4;
                     bf[B_NMP * 32 + j] = L.nmP;
-                    bf[B_SP * 32 + j] = L.sp;
                     bf[B_C * 32 + j] = L.C;
                     bi[B_N * 32 + j] = L.n;
                     bi[B_LEN * 32 + j] = len;
