@@ -9,15 +9,14 @@
 // sum of the stage speeds, with no multiply.  (s is rounded to binary32, so
 // the drag coefficient in effect is s^2, within 2e-7 relative of k.)
 // Speed and gap are carried as
-// unevaluated double-float pairs (hi + lo): each step's increment is added with
-// Fast2Sum and its rounding error kept in lo, so 1e4-1e5 increments of
-// 1e-3-1e-4 relative size do not lose the ~1e-7 relative precision of a
-// binary32 stage.  Each update is Fast2Sum of (hi, lo + increment), which keeps
-// the pair normalised (|lo| <= ulp(hi)/2): the stages read the speed's high word
-// (with lo left to grow, a nearly constant increment leaves the same rounding
-// residual every step and the stages see a biased speed), and a slow car's step
-// can be far below half an ulp of the gap.  Contact is g <= 0 on the pair; the TTC margin
-// (g + noise) - thr v is formed with the exact error of thr v.
+// unevaluated double-float pairs (hi + lo), so 1e4-1e5 increments of 1e-3-1e-4
+// relative size do not lose the ~1e-7 relative precision of a binary32 stage.
+// Within a window of steps the high words stay fixed and every increment is
+// added to the low word; the stages start from v1 = vh + vl, so they see the
+// current speed without bias, and a slow car's step, far below half an ulp of
+// the gap, still counts.  At the end of each window Fast2Sum folds the low
+// words back (|lo| <= ulp(hi)/2 again).  Contact is g <= 0 on the pair; the
+// TTC margin (g + noise) - thr v is formed with the exact error of thr v.
 //
 // Actuator (Eq. 6).  The lag is linear with the command u held over a step, so
 // the lane carries e = a - u: RK4's stage values are u + p_j e with p1 = 1,
@@ -266,74 +265,78 @@ struct Lane32 {
         ev = (trig && n_b >= n && n_b < n_last) ? n_b : n_last;
     }
 
-    // Common tail of a step: position / speed increments, compensated updates,
-    // actuator decay.  Returns the end-of-step pairs in the out-parameters.
-    __device__ __forceinline__ void advance(float q1, float q2, float q3, float q4, float v2,
-                                            float v3, float v4, float &g1h, float &g1l,
-                                            float &w1h, float &w1l, float &en) const
+    // One RK4 step inside the current piece of r(D) (one FMA per stage for r)
+    // or, with FULL_MIN, with the full minimum per stage.  Within a window
+    // the high words stay fixed and each step's increments are added to the
+    // low words (`normalize` folds them in at the end of the window): the
+    // stages start from v1 = vh + vl, so they see the current speed, and the
+    // gap's low word collects position increments far below half an ulp of
+    // the high word.  The gap scale sigma = s / h6 is built from the same
+    // binary32 factor nh6s = -s h6 as the speed update, so distance and speed
+    // advance with one step factor (independently rounded factors would scale
+    // every stopping distance by their ratio, a systematic ~5e-8 relative
+    // error), and the gap falls by exactly v1 + 2 v2 + 2 v3 + v4.  Returns the
+    // end-of-step low words and actuator deviation.
+    template <bool FULL_MIN>
+    __device__ __forceinline__ void rk4_step(float &vl1, float &gl1, float &en) const
     {
-        // The gap scale sigma = s / h6 is built from the same binary32 speed
-        // factor nh6s = -s h6, so distance and speed advance with one step
-        // factor (independently rounded factors would scale every stopping
-        // distance by their ratio, a systematic ~5e-8 relative error).  The
-        // stage speeds are formed from the high word, so lo enters with the
-        // full weight 1 + 2 + 2 + 1 = 6.
-        const float dx = fmaf(6.0f, vl, fmaf(2.0f, v2 + v3, vh + v4));
-        // Fast2Sum of (hi, lo + increment) keeps each pair normalised
-        const float tv = fmaf(nh6s, fmaf(2.0f, q2 + q3, q1 + q4), vl);
-        w1h = vh + tv;
-        w1l = tv - (w1h - vh);
-        const float tg = gl - dx;
-        g1h = gh + tg;
-        g1l = tg - (g1h - gh);
+        const float v1 = vh + vl;
+        const float q1 = fmaf(v1, v1, FULL_MIN ? rg_full(cf(L_NP1)) : fmaf(e, a1, C));
+        const float v2 = fmaf(nh2s, q1, v1);
+        const float q2 = fmaf(v2, v2, FULL_MIN ? rg_full(cf(L_NP2)) : fmaf(e, a2, C));
+        const float v3 = fmaf(nh2s, q2, v1);
+        const float q3 = fmaf(v3, v3, FULL_MIN ? rg_full(cf(L_NP3)) : fmaf(e, a3, C));
+        const float v4 = fmaf(ndts, q3, v1);
+        const float q4 = fmaf(v4, v4, FULL_MIN ? rg_full(cf(L_NP4)) : fmaf(e, a4, C));
+        vl1 = fmaf(nh6s, fmaf(2.0f, q2 + q3, q1 + q4), vl);
+        gl1 = gl - fmaf(2.0f, v2 + v3, v1 + v4);
         en = fmaf(nmP, e, e);
     }
 
-    __device__ __forceinline__ void commit(float g1h, float g1l, float w1h, float w1l, float en)
+    // Fold the low words into the high words (Fast2Sum; the pairs stay exact).
+    __device__ __forceinline__ void normalize()
     {
-        vh = w1h;
-        vl = w1l;
-        gh = g1h;
-        gl = g1l;
+        const float sv = vh + vl;
+        vl = vl - (sv - vh);
+        vh = sv;
+        const float sg = gh + gl;
+        gl = gl - (sg - gh);
+        gh = sg;
+    }
+
+    // Whether the state (vh, vl1), (gh, gl1) has stopped or reached the lead.
+    __device__ __forceinline__ bool terminal(float vl1, float gl1) const
+    {
+        return (LEAD && gh + gl1 <= 0.0f) || vh + vl1 <= 0.0f;
+    }
+
+    __device__ __forceinline__ void commit(float vl1, float gl1, float en)
+    {
+        vl = vl1;
+        gl = gl1;
         e = en;
         n = n + 1;
     }
 
-    // The end-of-step pairs and actuator deviation of a step inside the
-    // current piece of r(D): one FMA per stage for r.
-    __device__ __forceinline__ void piece_step(float &g1h, float &g1l, float &w1h, float &w1l,
-                                               float &en) const
-    {
-        const float q1 = fmaf(vh, vh, fmaf(e, a1, C));
-        const float v2 = fmaf(nh2s, q1, vh);
-        const float q2 = fmaf(v2, v2, fmaf(e, a2, C));
-        const float v3 = fmaf(nh2s, q2, vh);
-        const float q3 = fmaf(v3, v3, fmaf(e, a3, C));
-        const float v4 = fmaf(ndts, q3, vh);
-        const float q4 = fmaf(v4, v4, fmaf(e, a4, C));
-        advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
-    }
-
     // A checked step inside the current piece; true if the rollout ended
-    // (contact or stop) in this step, which is then not committed.
-    __device__ __forceinline__ bool step_fast(float &g1h, float &g1l, float &w1h, float &w1l)
+    // (contact or stop) in this step, which is then not committed (its
+    // end-of-step low words are returned).
+    __device__ __forceinline__ bool step_fast(float &vl1, float &gl1)
     {
         float en;
-        piece_step(g1h, g1l, w1h, w1l, en);
-        const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f;
-        if (!ended) commit(g1h, g1l, w1h, w1l, en);
+        rk4_step<false>(vl1, gl1, en);
+        const bool ended = terminal(vl1, gl1);
+        if (!ended) commit(vl1, gl1, en);
         return ended;
     }
 
     // An unchecked step inside the current piece (step counter not advanced).
     __device__ __forceinline__ void step_unchecked()
     {
-        float g1h, g1l, w1h, w1l, en;
-        piece_step(g1h, g1l, w1h, w1l, en);
-        vh = w1h;
-        vl = w1l;
-        gh = g1h;
-        gl = g1l;
+        float vl1, gl1, en;
+        rk4_step<false>(vl1, gl1, en);
+        vl = vl1;
+        gl = gl1;
         e = en;
     }
 
@@ -385,6 +388,7 @@ struct Lane32 {
 #pragma unroll 1
             for (int j = 0; j < len; ++j) step_unchecked();
         }
+        normalize();
         if ((LEAD && gh <= 0.0f) || vh <= 0.0f) {
             vh = vh0;
             vl = vl0;
@@ -411,25 +415,19 @@ struct Lane32 {
     // A step crossing a breakpoint of r(D), or the last step before the
     // horizon (which may also be the onset step): full minimum for r, then
     // re-select the piece.
-    __device__ __forceinline__ bool step_slow(const ModelF32 &F, int32_t n_last, float &g1h,
-                                              float &g1l, float &w1h, float &w1l)
+    __device__ __forceinline__ bool step_slow(const ModelF32 &F, int32_t n_last, float &vl1,
+                                              float &gl1)
     {
         if (n == ci(L_NB)) {  // the command switches on at the start of this step
             set_cf(L_U, F.acmd);
             e = e - F.acmd;
         }
-        const float q1 = fmaf(vh, vh, rg_full(cf(L_NP1)));
-        const float v2 = fmaf(nh2s, q1, vh);
-        const float q2 = fmaf(v2, v2, rg_full(cf(L_NP2)));
-        const float v3 = fmaf(nh2s, q2, vh);
-        const float q3 = fmaf(v3, v3, rg_full(cf(L_NP3)));
-        const float v4 = fmaf(ndts, q3, vh);
-        const float q4 = fmaf(v4, v4, rg_full(cf(L_NP4)));
         float en;
-        advance(q1, q2, q3, q4, v2, v3, v4, g1h, g1l, w1h, w1l, en);
-        const bool ended = (LEAD && g1h <= 0.0f) || w1h <= 0.0f || n >= n_last;
+        rk4_step<true>(vl1, gl1, en);
+        const bool ended = terminal(vl1, gl1) || n >= n_last;
         if (!ended) {
-            commit(g1h, g1l, w1h, w1l, en);
+            commit(vl1, gl1, en);
+            normalize();
             set_piece(-fmaf(-cf(L_NP1), e, cf(L_U)));
             next_event(n_last);
         }
@@ -575,14 +573,19 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.C = bf[B_C * 32 + j];
             R.n = bi[B_N * 32 + j];
             // ends within len steps: the window's last state is terminal
-            for (int s = 1; !R.step_fast(g1h, g1l, w1h, w1l) && s < len; ++s) {
+            float vl1, gl1;
+            for (int s = 1; !R.step_fast(vl1, gl1) && s < len; ++s) {
             }
             g0h = R.gh;
             g0l = R.gl;
             w0h = R.vh;
             w0l = R.vl;
+            g1h = R.gh;
+            g1l = gl1;
+            w1h = R.vh;
+            w1l = vl1;
             n1 = R.n + 1;
-            status = (LEAD && g1h <= 0.0f) ? AEB_CONTACT : AEB_STOP;
+            status = (LEAD && g1h + g1l <= 0.0f) ? AEB_CONTACT : AEB_STOP;
         } else {
             g0h = bf[B_GH * 32 + j];
             g0l = bf[B_GL * 32 + j];
@@ -679,7 +682,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
 
         // ---- one window of up to K RK4 steps (Sec. IV-D) per lane ----
         bool ended = false;
-        float g1h, g1l, w1h, w1l;
+        float vl1, gl1;  // end-of-step low words of a slow step that ended
         if (TTC && active && !L.trig) L.ttc_check(F, n_last);
         const bool onset = active && L.n == L.ev && L.n < n_last;
         if (__any_sync(kFull, onset)) {  // warp-uniform: once per rollout
@@ -687,7 +690,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         }
         const bool slow = active && ((L.n == L.ev) || (L.e < L.eth));
         if (__any_sync(kFull, slow)) {  // warp-uniform: rare
-            if (slow) ended = L.step_slow(F, n_last, g1h, g1l, w1h, w1l);
+            if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
         }
         const bool win = active && !slow;
         const int len = win ? L.window_len() : AEB_FP32_WINDOW;
@@ -731,13 +734,13 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     bi[B_N * 32 + j] = L.n;
                     bi[B_LEN * 32 + j] = len;
                 } else {
-                    bf[B_G1H * 32 + j] = g1h;
-                    bf[B_G1L * 32 + j] = g1l;
-                    bf[B_W1H * 32 + j] = w1h;
-                    bf[B_W1L * 32 + j] = w1l;
-                    bi[B_STATUS * 32 + j] = (LEAD && g1h <= 0.0f)
+                    bf[B_G1H * 32 + j] = L.gh;
+                    bf[B_G1L * 32 + j] = gl1;
+                    bf[B_W1H * 32 + j] = L.vh;
+                    bf[B_W1L * 32 + j] = vl1;
+                    bi[B_STATUS * 32 + j] = (LEAD && L.gh + gl1 <= 0.0f)
                                                 ? AEB_CONTACT
-                                                : (w1h <= 0.0f ? AEB_STOP : AEB_HORIZON);
+                                                : (L.vh + vl1 <= 0.0f ? AEB_STOP : AEB_HORIZON);
                     bi[B_N * 32 + j] = L.n + 1;
                     bi[B_LEN * 32 + j] = 0;
                 }
