@@ -88,6 +88,24 @@ struct ModelF32 {
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 
+// Relative margin on the actuator threshold of a window: covers the rounding
+// of K - 1 binary32 decays of e and of the power and quotient that form the
+// threshold.
+constexpr float kMargin = 1.00001f;
+
+// q^P by repeated squaring (P < 32, a compile-time constant).
+template <int P>
+__device__ __forceinline__ float powi(float q)
+{
+    float r = 1.0f, b = q;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        if ((P >> i) & 1) r *= b;
+        if ((P >> (i + 1)) != 0) b *= b;
+    }
+    return r;
+}
+
 // Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
 // warp's shared slab.
 template <bool LEAD, bool TTC>
@@ -221,24 +239,25 @@ struct Lane32 {
                 bb = b_[j];
             }
         }
+        // The breakpoint and the thresholds below only decide when a step
+        // must take the full minimum, so they use the fast binary32 quotient
+        // (error ~2 ulp, far inside the 1e-5 margin on e).
         float B = finf();
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (b_[j] < bb) B = fminf(B, (a_[j] - ab) / (bb - b_[j]));
+            if (b_[j] < bb && a_[j] < finf()) B = fminf(B, __fdividef(a_[j] - ab, bb - b_[j]));
         a1 = bb * cf(L_NP1);
         a2 = bb * cf(L_NP2);
         a3 = bb * cf(L_NP3);
         a4 = bb * cf(L_NP4);
         C = (ab - bb * u) + cf(L_GS);
-        eth = (p4 > 0.0f && B < finf()) ? (-u - B) / p4 : -finf();
+        eth = (p4 > 0.0f && B < finf()) ? __fdividef(-u - B, p4) : -finf();
         // e decays by (1 - mP) per step; a window of K steps stays inside the
         // piece if its last step does: e (1 - mP)^(K-1) >= eth (with margin)
         float ethK = eth;
         if (eth > 0.0f) {
-            float f = 1.0f;
-#pragma unroll
-            for (int j = 1; j < AEB_FP32_WINDOW; ++j) f *= (1.0f + nmP);
-            ethK = (f > 0.0f) ? (eth / f) * 1.000001f : finf();
+            const float f = powi<AEB_FP32_WINDOW - 1>(1.0f + nmP);
+            ethK = (f > 0.0f) ? __fdividef(eth, f) * kMargin : finf();
         }
         set_cf(L_ETHK, ethK);
     }
@@ -340,18 +359,25 @@ struct Lane32 {
         e = en;
     }
 
+    // Whether the next K steps may run as one window with no event among
+    // them (implies no onset and no slow step at this step).
+    __device__ __forceinline__ bool full_window_ok() const
+    {
+        return (!TTC || trig) && n + AEB_FP32_WINDOW <= ev && !(e < cf(L_ETHK));
+    }
+
     // How many steps (1 .. K) may run as one window from here: none of them
     // a slow step, the trigger (if any) already fired, and the piece of r(D)
     // valid for each (the actuator deviation e, which decays by the factor
-    // q = 1 - mP per step, stays >= eth at the start of every step; the 1e-6
-    // margin covers the rounding of the decays).
+    // q = 1 - mP per step, stays >= eth at the start of every step, with the
+    // margin kMargin).
     __device__ __forceinline__ int window_len() const
     {
         if (TTC && !trig) return 1;
         const int32_t room = ev - n;  // >= 1: a lane at its event takes the slow path
         int len = room < AEB_FP32_WINDOW ? (int)room : AEB_FP32_WINDOW;
         if (e < cf(L_ETHK)) {  // close to a breakpoint (eth > 0 here)
-            const float q = 1.0f + nmP, m = eth * 1.000001f;
+            const float q = 1.0f + nmP, m = eth * kMargin;
             int lb = 1;
             if (q > 0.0f && q < 1.0f) {
                 const float q2 = q * q, q3 = q2 * q;
@@ -684,18 +710,27 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         bool ended = false;
         float vl1, gl1;  // end-of-step low words of a slow step that ended
         if (TTC && active && !L.trig) L.ttc_check(F, n_last);
-        const bool onset = active && L.n == L.ev && L.n < n_last;
-        if (__any_sync(kFull, onset)) {  // warp-uniform: once per rollout
-            if (onset) L.onset_event(F, n_last);
-        }
-        const bool slow = active && ((L.n == L.ev) || (L.e < L.eth));
-        if (__any_sync(kFull, slow)) {  // warp-uniform: rare
-            if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
+        // Most passes: every active lane can run a full window (no event in
+        // reach); one vote decides.  Otherwise handle onsets, slow steps and
+        // window lengths lane by lane.
+        bool full = __all_sync(kFull, !active || L.full_window_ok());
+        bool slow = false;
+        int len = AEB_FP32_WINDOW;
+        if (!full) {
+            const bool onset = active && L.n == L.ev && L.n < n_last;
+            if (__any_sync(kFull, onset)) {  // warp-uniform: once per rollout
+                if (onset) L.onset_event(F, n_last);
+            }
+            slow = active && ((L.n == L.ev) || (L.e < L.eth));
+            if (__any_sync(kFull, slow)) {  // warp-uniform: rare
+                if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
+            }
+            if (active && !slow) len = L.window_len();
+            full = __all_sync(kFull, len == AEB_FP32_WINDOW);
         }
         const bool win = active && !slow;
-        const int len = win ? L.window_len() : AEB_FP32_WINDOW;
         bool replay = false;
-        if (__all_sync(kFull, len == AEB_FP32_WINDOW)) {
+        if (full) {
             if (win) replay = L.template step_window<true>(len);
         } else {
             if (win) replay = L.template step_window<false>(len);
