@@ -126,6 +126,20 @@ OutDev out_dev(const aeb_outputs *o)
     return d;
 }
 
+// The output columns from row `off` on (NULL columns stay NULL).
+OutDev offset_out(const OutDev &o, uint64_t off)
+{
+    OutDev d = o;
+    if (d.status) d.status += off;
+    if (d.x_raw) d.x_raw += off;
+    if (d.x_ref) d.x_ref += off;
+    if (d.v_imp) d.v_imp += off;
+    if (d.t_end) d.t_end += off;
+    if (d.n_steps) d.n_steps += off;
+    if (d.n_onset) d.n_onset += off;
+    return d;
+}
+
 namespace {
 
 // Library scratch, one region per (device, stream): work on one stream is
@@ -197,11 +211,33 @@ aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &
     return AEB_OK;
 }
 
-// Device buffers of aeb_evaluate, one set per (device, stream).
+// Device buffers, streams and events of aeb_evaluate, one set per (device,
+// stream).  The parameter upload is cut into chunks: chunk k is copied on
+// `copy` while chunk k - 1 rolls out on comp[(k - 1) % 2], so the copies hide
+// behind the arithmetic, and two compute streams let a chunk's launch start
+// while the previous one drains its last rollouts.
+constexpr int kEvalMaxChunks = 8;
+constexpr uint64_t kEvalMinChunk = uint64_t(1) << 20;
 struct EvalBuffers {
     void *base = nullptr;
     uint64_t cap = 0;  // samples
+    cudaStream_t copy = nullptr, comp[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, copied[kEvalMaxChunks] = {}, done[2] = {nullptr, nullptr};
 };
+
+cudaError_t eval_streams(EvalBuffers &b)
+{
+    if (b.copy) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&b.copy, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&b.comp[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.start, cudaEventDisableTiming);
+    for (int i = 0; i < kEvalMaxChunks && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&b.copied[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&b.done[i], cudaEventDisableTiming);
+    return e;
+}
 std::map<std::pair<int, uintptr_t>, EvalBuffers> g_eval;
 
 constexpr size_t kEvalBytesPerSample = 8 * AEB_NFIELDS + 1 + 8 * 4 + 4 * 2;
@@ -295,9 +331,13 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     void *base = nullptr;
+    EvalBuffers *eb = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
         EvalBuffers &b = g_eval[{dev, reinterpret_cast<uintptr_t>(s)}];
+        e = eval_streams(b);
+        if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: streams");
+        eb = &b;
         if (b.cap < cap) {
             if (b.base) {
                 e = cudaStreamSynchronize(s);
@@ -323,13 +363,7 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
     aeb_params dp;
     double **dcols[AEB_NFIELDS] = {&dp.v0, &dp.d0, &dp.mu, &dp.gs, &dp.gc,
                                    &dp.mass, &dp.cd, &dp.tau, &dp.t_delay, &dp.noise};
-    for (int j = 0; j < AEB_NFIELDS; ++j) {
-        *dcols[j] = reinterpret_cast<double *>(take(8 * cap));
-        if (n > 0) {
-            e = cudaMemcpyAsync(*dcols[j], hp.col[j], 8 * n, cudaMemcpyHostToDevice, s);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(params)");
-        }
-    }
+    for (int j = 0; j < AEB_NFIELDS; ++j) *dcols[j] = reinterpret_cast<double *>(take(8 * cap));
     aeb_outputs dout;
     dout.status = reinterpret_cast<uint8_t *>(take(cap));
     dout.x_raw = reinterpret_cast<double *>(take(8 * cap));
@@ -346,8 +380,35 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
         if (!host_out || !host_out->x_raw) want.x_raw = nullptr;
         if (!host_out || !host_out->t_end) want.t_end = nullptr;
         if (!host_out || !host_out->n_onset) want.n_onset = nullptr;
-        st = rollout_impl(md, pd, n, precision, out_dev(&want), s);
-        if (st != AEB_OK) return st;
+        const OutDev od = out_dev(&want);
+        uint64_t chunks = (n + kEvalMinChunk - 1) / kEvalMinChunk;
+        if (chunks > (uint64_t)kEvalMaxChunks) chunks = kEvalMaxChunks;
+        const uint64_t per = (n + chunks - 1) / chunks;
+        // the copies start after the work already queued on the caller's stream
+        e = cudaEventRecord(eb->start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(eb->copy, eb->start, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: stream order");
+        for (uint64_t k = 0; k < chunks; ++k) {
+            const uint64_t off = k * per, len = (off + per <= n) ? per : n - off;
+            ParamsDev pk = pd;
+            for (int j = 0; j < AEB_NFIELDS; ++j) {
+                e = cudaMemcpyAsync(const_cast<double *>(pd.col[j]) + off, hp.col[j] + off, 8 * len,
+                                    cudaMemcpyHostToDevice, eb->copy);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(params)");
+                pk.col[j] = pd.col[j] + off;
+            }
+            cudaStream_t cs = eb->comp[k % 2];
+            e = cudaEventRecord(eb->copied[k], eb->copy);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, eb->copied[k], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: chunk order");
+            st = rollout_impl(md, pk, len, precision, offset_out(od, off), cs);
+            if (st != AEB_OK) return st;
+        }
+        for (int i = 0; i < 2; ++i) {
+            e = cudaEventRecord(eb->done[i], eb->comp[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, eb->done[i], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: join");
+        }
     }
     st = reduce_impl(&dout, n, *hist, dstats, s);
     if (st != AEB_OK) return st;

@@ -255,6 +255,26 @@ def test_evaluate_host_path(aeb, oracle_mod):
     assert bytes(st2) == bytes(st)
 
 
+def test_evaluate_chunked_upload(aeb):
+    """aeb_evaluate above 2^20 samples uploads and rolls out in chunks on
+    internal streams; its outputs and statistics are byte-identical to one
+    device-resident rollout and reduction of the same parameters."""
+    m = ai.single_model()
+    n = 2_500_003  # three chunks, ragged last one
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=41), 0, n)
+    which = ("status", "x_ref", "v_imp", "n_steps", "n_onset")
+    host_out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in which}
+    st = aeb.aeb_evaluate(m, p, n, aeb.FP32_COMP, aeb.hist_spec(), host_out=host_out)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n, which=which)
+    aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+    S = aeb.alloc_stats()
+    aeb.aeb_reduce(O, n, aeb.hist_spec(), S)
+    for k in which:
+        assert np.array_equal(host_out[k].view(np.uint8), O[k].cpu().numpy().view(np.uint8)), k
+    assert bytes(st) == bytes(S.cpu().numpy())
+
+
 def test_full_size_sampled(aeb, oracle_mod):
     """The single-scenario workload at N = 1e7 in the benchmark's launch
     configuration: sampled outputs against the oracle, and invariants over
