@@ -48,7 +48,12 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
 # DRAM bytes per sample of the FP32 rollout kernel, from one ncu capture at
 # N = 2e6 (183.7 MB per launch); traffic grows in proportion to the samples.
-FP32_TRAFFIC_BYTES_PER_SAMPLE = 183.657216e6 / 2e6
+FP32_TRAFFIC_BYTES_PER_SAMPLE = 183.511296e6 / 2e6
+# binary32 thread instructions the FP32 kernel executes per RK4 lane-step on this
+# workload (ncu smsp__inst_executed x thread_inst_executed_per_inst_executed at
+# N = 2e6, same profile); the issue-slot view of the roofline
+FP32_THREAD_INST_PER_STEP = 27.4
+FP32_ISSUE_PEAK = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6  # lane-instructions/s
 
 
 def parse():
@@ -406,7 +411,16 @@ def main():
                                        "scaled by samples",
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (unit counts, max clock)",
                      "flops_per_launch": steps_per_launch * FLOPS_PER_STEP,
-                     "launch_ms": roll_ms},
+                     "launch_ms": roll_ms,
+                     "note": "flops counted from the 73-op binary64 definition of a step; the "
+                             "kernel runs ~21 fused binary32 instructions per step, so frac "
+                             "may exceed 1 without skipped work",
+                     "issue": {"thread_inst_per_step": FP32_THREAD_INST_PER_STEP,
+                               "achieved": steps_per_launch * FP32_THREAD_INST_PER_STEP
+                                           / (roll_ms / 1e3),
+                               "peak": FP32_ISSUE_PEAK, "unit": "lane-instructions/s",
+                               "frac": steps_per_launch * FP32_THREAD_INST_PER_STEP
+                                       / (roll_ms / 1e3) / FP32_ISSUE_PEAK}},
         "kernels_ms": {"rollout_fp32": roll_ms, "reduce": red_ms},
         "measured_pipe_peaks": {"fp32_fma_tflops": peaks[0], "fp64_fma_tflops": peaks[1],
                                 "fp64_add_tops": peaks[2],
