@@ -73,13 +73,18 @@ constexpr int kThreads = 32 * kWarps;
 #define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
 #endif
 
-// prepared per-sample record, stored field-major in shared memory
+// prepared per-sample record, stored field-major in shared memory (the TTC
+// fields exist only in the TTC-trigger kernel; -s dt = 2 (-s dt/2) exactly,
+// p4 = -np4 and np1 = -1 when tau > 0, else 0, are derived where needed)
 enum {
-    R_W0H, R_W0L, R_G0H, R_G0L, R_GS, R_S, R_NH2S, R_NDTS, R_NH6S, R_F0, R_F1, R_R0,
-    R_R1, R_MG, R_NP1, R_NP2, R_NP3, R_NP4, R_P4, R_NMP, R_NZ, R_THRH, R_THRL,
-    R_NF  // float fields
+    R_W0H, R_W0L, R_G0H, R_G0L, R_GS, R_S, R_NH2S, R_NH6S, R_F0, R_F1, R_R0, R_R1, R_MG,
+    R_NP2, R_NP3, R_NP4, R_NMP,
+    R_NF_BASE,                                   // float fields of every kernel
+    R_NZ = R_NF_BASE, R_THRH, R_THRL, R_NF_TTC   // TTC trigger only
 };
 enum { R_NDELAY, R_KIND, R_NI };  // int fields
+template <bool TTC>
+__host__ __device__ constexpr int rec_floats() { return TTC ? R_NF_TTC : R_NF_BASE; }
 enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 
 struct ModelF32 {
@@ -144,7 +149,6 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         tf[R_GS * T + j] = __double2float_rn(f[kGs]);
         tf[R_S * T + j] = sc;
         tf[R_NH2S * T + j] = __double2float_rn(-(sd * M.h2));
-        tf[R_NDTS * T + j] = __double2float_rn(-(sd * M.dt));
         tf[R_NH6S * T + j] = nh6s;
         const double mu = f[kMu], mh = mu * M.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
@@ -164,19 +168,15 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         if (f[kTau] > 0.0) {
             const double z = M.dt / f[kTau];
             const double p4 = 1.0 - z + 0.5 * z * z - 0.25 * z * z * z;
-            tf[R_NP1 * T + j] = -1.0f;
             tf[R_NP2 * T + j] = __double2float_rn(-(1.0 - 0.5 * z));
             tf[R_NP3 * T + j] = __double2float_rn(-(1.0 - 0.5 * z + 0.25 * z * z));
             tf[R_NP4 * T + j] = __double2float_rn(-p4);
-            tf[R_P4 * T + j] = __double2float_rn(p4);
             tf[R_NMP * T + j] =
                 __double2float_rn(-(z * (1.0 + z * (-0.5 + z * (1.0 / 6.0 - z / 24.0)))));
         } else {
-            tf[R_NP1 * T + j] = 0.0f;
             tf[R_NP2 * T + j] = 0.0f;
             tf[R_NP3 * T + j] = 0.0f;
             tf[R_NP4 * T + j] = 0.0f;
-            tf[R_P4 * T + j] = 0.0f;
             tf[R_NMP * T + j] = -1.0f;
         }
         if (TTC) {  // (g + noise) - thr v scaled by sigma: G + sigma noise - (sigma thr / s) w
@@ -193,11 +193,13 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 // test, records) live in a column of the warp's shared slab, field-major with
 // stride 32, to keep the step loop's register budget small.
 enum {
-    L_F0, L_F1, L_R0, L_R1, L_MG, L_P4, L_GS, L_U, L_NZ, L_THRH, L_THRL, L_S, L_ETHK,  // floats
-    L_NP1, L_NP2, L_NP3, L_NP4,
-    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                 // ints
-    L_NW
+    L_F0, L_F1, L_R0, L_R1, L_MG, L_GS, L_U, L_S, L_ETHK, L_NP1, L_NP2, L_NP3, L_NP4,  // floats
+    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                             // ints
+    L_NW_BASE,
+    L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NW_TTC  // TTC trigger only (floats)
 };
+template <bool TTC>
+__host__ __device__ constexpr int cold_fields() { return TTC ? L_NW_TTC : L_NW_BASE; }
 
 template <bool LEAD, bool TTC>
 struct Lane32 {
@@ -226,7 +228,7 @@ struct Lane32 {
     // D4 = -(u + p4 e) exceeds B.
     __device__ __forceinline__ void set_piece(float D)
     {
-        const float u = cf(L_U), p4 = cf(L_P4);
+        const float u = cf(L_U), p4 = -cf(L_NP4);
         const float a_[4] = {0.0f, cf(L_F0), cf(L_R0), cf(L_MG)};
         const float b_[4] = {1.0f, cf(L_F1), cf(L_R1), 0.0f};
         float ab = 0.0f, bb = 1.0f, bv = D;
@@ -505,9 +507,10 @@ struct Lane32 {
         gh = tf[R_G0H * T + slot];
         gl = tf[R_G0L * T + slot];
         nh2s = tf[R_NH2S * T + slot];
-        ndts = tf[R_NDTS * T + slot];
+        ndts = 2.0f * nh2s;
         nh6s = tf[R_NH6S * T + slot];
-        set_cf(L_NP1, tf[R_NP1 * T + slot]);
+        // np1 = -1 when tau > 0 (then np2 or np3 is nonzero), else 0
+        set_cf(L_NP1, (tf[R_NP2 * T + slot] != 0.0f || tf[R_NP3 * T + slot] != 0.0f) ? -1.0f : 0.0f);
         set_cf(L_NP2, tf[R_NP2 * T + slot]);
         set_cf(L_NP3, tf[R_NP3 * T + slot]);
         set_cf(L_NP4, tf[R_NP4 * T + slot]);
@@ -518,7 +521,6 @@ struct Lane32 {
         set_cf(L_R0, tf[R_R0 * T + slot]);
         set_cf(L_R1, tf[R_R1 * T + slot]);
         set_cf(L_MG, tf[R_MG * T + slot]);
-        set_cf(L_P4, tf[R_P4 * T + slot]);
         set_cf(L_S, tf[R_S * T + slot]);
         set_ci(L_NDELAY, n_delay);
         set_ci(L_PIDXLO, (int)(uint32_t)pi);
@@ -548,18 +550,22 @@ struct Lane32 {
 // (end pairs in the B_A1 .. B_A4 slots) and its status.  Both keep the
 // scales s (B_S) and -s h6 (B_NH6S) that undo the scaled units.
 enum {
-    B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NDTS, B_NH6S, B_A1, B_A2, B_A3, B_A4, B_NMP,
+    B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NH6S, B_A1, B_A2, B_A3, B_A4, B_NMP,
     B_C, B_S, B_NF
 };
 enum { B_G1H = B_A1, B_G1L = B_A2, B_W1H = B_A3, B_W1L = B_A4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
-constexpr int kColdWords = L_NW * 32;
+template <bool TTC>
 __host__ __device__ constexpr int warp_words(int T)
 {
-    return (R_NF + R_NI) * T + kBatchWords + kColdWords;
+    return (rec_floats<TTC>() + R_NI) * T + kBatchWords + cold_fields<TTC>() * 32;
 }
-__host__ __device__ constexpr size_t smem_per_block(int T) { return sizeof(float) * warp_words(T) * kWarps; }
+template <bool TTC>
+__host__ __device__ constexpr size_t smem_per_block(int T)
+{
+    return sizeof(float) * warp_words<TTC>(T) * kWarps;
+}
 
 // For the warp's queued records, all 32 lanes at once: replay the windows that
 // contained an end one checked step at a time, then the binary64 refinement
@@ -589,7 +595,7 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.gl = bf[B_GL * 32 + j];
             R.e = bf[B_E * 32 + j];
             R.nh2s = bf[B_NH2S * 32 + j];
-            R.ndts = bf[B_NDTS * 32 + j];
+            R.ndts = 2.0f * R.nh2s;
             R.nh6s = bf[B_NH6S * 32 + j];
             R.a1 = bf[B_A1 * 32 + j];
             R.a2 = bf[B_A2 * 32 + j];
@@ -655,9 +661,9 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     extern __shared__ float smem[];
     const unsigned lane = threadIdx.x & 31u;
     const int T = (int)W.tile;
-    float *tf = smem + (threadIdx.x >> 5) * warp_words(T);
-    int *ti = reinterpret_cast<int *>(tf + R_NF * T);
-    float *bf = tf + (R_NF + R_NI) * T;
+    float *tf = smem + (threadIdx.x >> 5) * warp_words<TTC>(T);
+    int *ti = reinterpret_cast<int *>(tf + rec_floats<TTC>() * T);
+    float *bf = tf + (rec_floats<TTC>() + R_NI) * T;
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
     float *coldw = bf + kBatchWords;
     const int32_t n_last = M.n_max - 1;
@@ -759,7 +765,6 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 if (replay) {
                     bf[B_E * 32 + j] = L.e;
                     bf[B_NH2S * 32 + j] = L.nh2s;
-                    bf[B_NDTS * 32 + j] = L.ndts;
                     bf[B_A1 * 32 + j] = L.a1;
                     bf[B_A2 * 32 + j] = L.a2;
                     bf[B_A3 * 32 + j] = L.a3;
@@ -800,7 +805,7 @@ cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, con
     auto kern = k_rollout_fp32<LEAD, TTC>;
     const int T = w.tiles ? (int)w.tile : (cfg.tile > 0 ? cfg.tile : kTileDefault);
     if (T < 32 || T > kTileMax || T % 32) return cudaErrorInvalidValue;
-    const size_t smem = smem_per_block(T);
+    const size_t smem = smem_per_block<TTC>(T);
     int dev = 0, sms = 0, per_sm = cfg.blocks_per_sm;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
