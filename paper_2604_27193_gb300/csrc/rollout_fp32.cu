@@ -363,21 +363,22 @@ struct Lane32 {
 
     // Whether the next K steps may run as one window with no event among
     // them (implies no onset and no slow step at this step).
-    __device__ __forceinline__ bool full_window_ok() const
+    __device__ __forceinline__ bool full_window_ok(int tlen) const
     {
-        return (!TTC || trig) && n + AEB_FP32_WINDOW <= ev && !(e < cf(L_ETHK));
+        return (!TTC || trig || tlen >= AEB_FP32_WINDOW) && n + AEB_FP32_WINDOW <= ev &&
+               !(e < cf(L_ETHK));
     }
 
     // How many steps (1 .. K) may run as one window from here: none of them
-    // a slow step, the trigger (if any) already fired, and the piece of r(D)
+    // a slow step, none a possible TTC trigger (tlen), and the piece of r(D)
     // valid for each (the actuator deviation e, which decays by the factor
     // q = 1 - mP per step, stays >= eth at the start of every step, with the
     // margin kMargin).
-    __device__ __forceinline__ int window_len() const
+    __device__ __forceinline__ int window_len(int tlen) const
     {
-        if (TTC && !trig) return 1;
         const int32_t room = ev - n;  // >= 1: a lane at its event takes the slow path
         int len = room < AEB_FP32_WINDOW ? (int)room : AEB_FP32_WINDOW;
+        if (TTC && !trig && tlen < len) len = tlen;
         if (e < cf(L_ETHK)) {  // close to a breakpoint (eth > 0 here)
             const float q = 1.0f + nmP, m = eth * kMargin;
             int lb = 1;
@@ -464,20 +465,34 @@ struct Lane32 {
 
     // TTC trigger (while not yet triggered): (g + noise) - thr v <= 0, with the
     // exact rounding error of thr * vh; braking starts n_delay steps later.
-    __device__ __forceinline__ void ttc_check(const ModelF32 &F, int32_t n_last)
+    // Returns how many steps (1 .. K) may run before the next test: before
+    // the trigger the car coasts, the stage accelerations are q = w^2 + C >= C,
+    // so over a window the scaled speed stays below W = w + K s dt max(0, -C)
+    // and the margin falls by at most 6 W + thr' s dt max(0, -C) per step
+    // (the gap by the stage-speed sum, the speed term by the speed gain); the
+    // first L - 1 steps after this one cannot trigger while (L - 1) times that
+    // bound stays below the margin.
+    __device__ __forceinline__ int ttc_check(const ModelF32 &F, int32_t n_last)
     {
         const float thr_h = cf(L_THRH);
         const float p = thr_h * vh;
         const float pe = fmaf(thr_h, vh, -p);
         const float hi = gh - p;
         const float lo = (gl + cf(L_NZ)) - (pe + fmaf(thr_h, vl, cf(L_THRL) * vh));
-        if (hi + lo <= 0.0f) {
+        const float m = hi + lo;
+        if (m <= 0.0f) {
             trig = true;
             const long long nb = (long long)n + ci(L_NDELAY);
             const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
             set_ci(L_NB, n_b);
             ev = (n_b < n_last) ? n_b : n_last;
+            return AEB_FP32_WINDOW;
         }
+        const float sdt = -ndts, acc = fmaxf(0.0f, -C);
+        const float W = fmaf((float)AEB_FP32_WINDOW * sdt, acc, vh + vl);
+        const float d = fmaf(6.0f, W, thr_h * sdt * acc) * 1.001f;
+        const float r = __fdividef(m, d) * 0.999f;
+        return r >= (float)(AEB_FP32_WINDOW - 1) ? AEB_FP32_WINDOW : 1 + (int)r;
     }
 
     // Load sample `slot` of the warp's tile (parameter row pi, output row i);
@@ -715,11 +730,12 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         // ---- one window of up to K RK4 steps (Sec. IV-D) per lane ----
         bool ended = false;
         float vl1, gl1;  // end-of-step low words of a slow step that ended
-        if (TTC && active && !L.trig) L.ttc_check(F, n_last);
+        int tlen = AEB_FP32_WINDOW;  // steps before the next TTC test
+        if (TTC && active && !L.trig) tlen = L.ttc_check(F, n_last);
         // Most passes: every active lane can run a full window (no event in
         // reach); one vote decides.  Otherwise handle onsets, slow steps and
         // window lengths lane by lane.
-        bool full = __all_sync(kFull, !active || L.full_window_ok());
+        bool full = __all_sync(kFull, !active || L.full_window_ok(tlen));
         bool slow = false;
         int len = AEB_FP32_WINDOW;
         if (!full) {
@@ -731,7 +747,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
             if (__any_sync(kFull, slow)) {  // warp-uniform: rare
                 if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
             }
-            if (active && !slow) len = L.window_len();
+            if (active && !slow) len = L.window_len(tlen);
             full = __all_sync(kFull, len == AEB_FP32_WINDOW);
         }
         const bool win = active && !slow;
