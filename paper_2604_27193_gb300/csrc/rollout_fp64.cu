@@ -9,6 +9,17 @@
 // in the same operation order as the binary64 definition, so each output is
 // the same bits (Sec. V-D: same samples, same integrator, same precision,
 // same termination, no fused or approximate operations).
+//
+// The realised deceleration is the minimum of lines (D, mu g cos(theta) and
+// the two axle lines, or D and the Eq. 5 cap), and a minimum returns one of
+// its arguments unchanged.  So a lane keeps the line that is the strict
+// minimum over an interval [dlo, dhi] of demand, shrunk at each end by a band
+// of 1e-12 relative (far above the few-ulp rounding of a line value, so no
+// rounding can change which line is smallest inside it); while a step's
+// stage demands lie in the interval (the first stage has the smallest demand
+// and the fourth the largest when dt / tau <= 2), each stage evaluates only
+// that line, with the same expression as the full minimum, and the result
+// is the same bits.  Other steps evaluate the full minimum and re-select.
 #include <climits>
 
 #include "rollout_common.cuh"
@@ -20,13 +31,73 @@ __device__ __forceinline__ double dmin(double a, double b) { return (b < a) ? b 
 
 struct NoExtra {};
 
+__device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000ll); }
+
 template <int CAP, bool LEAD, bool TTC>
 struct Lane64 {
     double x, v, a;
     double d0, gs, noise, k, it, thr;
     double mg, f0, f1, r0, r1, cap;
+    double pa, pb, dlo, dhi;      // current line pa + pb D (piece 1, 2) and its interval
     int32_t n, n_b, n_delay;
-    bool trig, lagged;
+    int piece;                    // 0: D, 1, 2: an axle line, 3: the constant cap; -1: none
+    bool trig, lagged, ordered;
+
+    // Select the line that is the strict minimum at demand D and the demand
+    // interval, shrunk by the band, on which it stays so (piece -1 if D is
+    // inside a band, lines are nearly parallel, or the stage demands are not
+    // ordered).
+    __device__ void select_piece(double D)
+    {
+        piece = -1;
+        if (!ordered) return;
+        double A[4], S[4];
+        int nl;
+        if (CAP == AEB_CAP_LUMPED) {
+            A[0] = 0.0; S[0] = 1.0; A[1] = cap; S[1] = 0.0;
+            nl = 2;
+        } else {
+            A[0] = 0.0; S[0] = 1.0; A[1] = f0; S[1] = f1; A[2] = r0; S[2] = r1; A[3] = mg; S[3] = 0.0;
+            nl = 4;
+        }
+        double val[4];
+        int cur = 0;
+        for (int j = 0; j < nl; ++j) {
+            val[j] = (j == 0) ? D : A[j] + S[j] * D;
+            if (val[j] < val[cur]) cur = j;
+        }
+        double lo = -dinf(), hi = dinf();
+        for (int j = 0; j < nl; ++j) {
+            if (j == cur) continue;
+            const double ds = S[cur] - S[j];
+            if (!(fabs(ds) >= 1e-6) || !(val[j] > val[cur])) return;
+            const double B = (A[j] - A[cur]) / ds;  // line j meets the current line
+            const double band = 1e-12 * (1.0 + fabs(A[j]) + fabs(A[cur]) + fabs(B)) / fabs(ds);
+            if (ds > 0.0) hi = fmin(hi, B - band);  // line j is below beyond B
+            else lo = fmax(lo, B + band);
+        }
+        if (!(lo <= D && D <= hi)) return;
+        dlo = lo;
+        dhi = hi;
+        if (CAP == AEB_CAP_LUMPED) {
+            piece = (cur == 0) ? 0 : 3;
+        } else {
+            piece = cur;
+            pa = A[cur];
+            pb = S[cur];
+        }
+    }
+
+    // dv/dt on the current piece: the same value as `accel` for D in the
+    // piece's interval.  `lines`: some lane of the warp is on an axle line.
+    __device__ __forceinline__ double accel_piece(double vv, double aa, bool lines) const
+    {
+        const double D = -aa;
+        const double c = (CAP == AEB_CAP_LUMPED) ? cap : mg;
+        double r = (piece == 0) ? D : c;
+        if (CAP != AEB_CAP_LUMPED && lines && (piece == 1 || piece == 2)) r = pa + pb * D;
+        return ((-r) - (k * vv) * vv) - gs;
+    }
 
     // Realised deceleration r for demand D = -a (Eq. 5 as printed, or the
     // per-axle fixed point min(min(D, mu gc), min(f0 + f1 D, r0 + r1 D))),
@@ -67,6 +138,7 @@ struct Lane64 {
         k = ((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]);
         lagged = f[kTau] > 0.0;
         it = lagged ? 1.0 / f[kTau] : 0.0;
+        ordered = !lagged || M.dt * it <= 2.0;
         const double mu = f[kMu], gc = f[kGc];
         const double mh = mu * M.hl;
         if (CAP == AEB_CAP_LUMPED) {
@@ -98,6 +170,7 @@ struct Lane64 {
         v = f[kV0];
         a = 0.0;
         n = 0;
+        select_piece(-a);
         return false;
     }
 
@@ -128,13 +201,32 @@ struct Lane64 {
         } else {
             a1 = a2 = a3 = a4 = u;
         }
-        const double kv1 = accel(v, a1);
-        const double v2 = v + h2 * kv1;
-        const double kv2 = accel(v2, a2);
-        const double v3 = v + h2 * kv2;
-        const double kv3 = accel(v3, a3);
-        const double v4 = v + dt * kv3;
-        const double kv4 = accel(v4, a4);
+        // With dt / tau <= 2 the stage demands lie between the first and the
+        // fourth (-a1 smallest when the command is a deceleration, so that
+        // a - u >= 0 from the start, -a4 smallest otherwise): two tests for
+        // the step.
+        const bool dec = M.a_cmd <= 0.0;
+        const double dfirst = dec ? -a1 : -a4, dlast = dec ? -a4 : -a1;
+        const bool pw = piece >= 0 && dfirst >= dlo && dlast <= dhi;
+        const bool lines = __any_sync(__activemask(), pw && (piece == 1 || piece == 2));
+        double kv1, kv2, kv3, kv4, v2, v3, v4;
+        if (pw) {
+            kv1 = accel_piece(v, a1, lines);
+            v2 = v + h2 * kv1;
+            kv2 = accel_piece(v2, a2, lines);
+            v3 = v + h2 * kv2;
+            kv3 = accel_piece(v3, a3, lines);
+            v4 = v + dt * kv3;
+            kv4 = accel_piece(v4, a4, lines);
+        } else {
+            kv1 = accel(v, a1);
+            v2 = v + h2 * kv1;
+            kv2 = accel(v2, a2);
+            v3 = v + h2 * kv2;
+            kv3 = accel(v3, a3);
+            v4 = v + dt * kv3;
+            kv4 = accel(v4, a4);
+        }
 
         const double xn = x + h6 * (((v + 2.0 * v2) + 2.0 * v3) + v4);
         const double vn = v + h6 * (((kv1 + 2.0 * kv2) + 2.0 * kv3) + kv4);
@@ -160,6 +252,7 @@ struct Lane64 {
         v = vn;
         a = an;
         n = n + 1;
+        if (!pw) select_piece(-a);
         return false;
     }
 };
