@@ -15,6 +15,11 @@ through aeb_evaluate (pinned host parameters in, host stats out, copies in
 the timed region).  The inputs (800 MB of parameters) exceed the 129 MB L2,
 so no flush is needed between steps.
 
+Beside the headline the line carries the serving run (Poisson requests,
+latency percentiles), the scenario-grid batched run, the TTC-threshold sweep and
+a coarse-step study (the same samples at dt = 0.1 .. 20 ms: speed and the error
+against the 0.1 ms rollouts); `--no-extras` skips the last three.
+
 `--impl reference` times the plain CPU oracle on a bounded sample of the same
 workload on the host cores (the CPU baseline), with the same metric.
 """
@@ -239,6 +244,54 @@ def sweep_run(aeb):
             "p_contact_ci95_at": pick, "precision": "fp32-compensated"}
 
 
+def dt_study(aeb, torch):
+    """Coarse-step fidelity and speed: the same 1e6 samples of the single-scenario
+    workload rolled out (FP32-compensated) at dt = 0.1 ms (the reference) and at
+    0.5 to 20 ms.  Per dt: launch time, rollouts/s, P(contact), mean stopping
+    distance, mean impact speed, and against the reference the share of samples
+    whose outcome (stop / contact) changed and the stopping-distance and
+    impact-speed differences of samples with the same outcome.  The brake onset
+    is quantised to the step (n dt >= t_delay), so part of the error is O(dt)."""
+    N = 1_000_000
+    sc = ai.single_scenario(seed=0)
+    p = aeb.aeb_sample_params(ai.single_model(), sc, 0, N)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    which = ("status", "x_ref", "v_imp", "n_steps")
+    res, ref = [], None
+    for dt in (1e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2, 2e-2):
+        m = ai.single_model(dt=dt)
+        O = aeb.alloc_outputs(N, which=which)
+        aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        o = {k: v.cpu().numpy() for k, v in O.items()}
+        stop, cont = o["status"] == 0, o["status"] == 1
+        row = {"dt_ms": dt * 1e3, "ms": ms, "rollouts_per_s": N / (ms / 1e3),
+               "steps_per_rollout": float(o["n_steps"].mean()),
+               "p_contact": float(cont.mean()), "mean_d_stop_m": float(o["x_ref"][stop].mean()),
+               "mean_v_imp_mps": float(o["v_imp"][cont].mean())}
+        if ref is None:
+            ref = o
+        else:
+            bs = stop & (ref["status"] == 0)
+            bc = cont & (ref["status"] == 1)
+            dd = np.abs(o["x_ref"][bs] - ref["x_ref"][bs])
+            dv = np.abs(o["v_imp"][bc] - ref["v_imp"][bc])
+            row.update({"outcome_changed": float((o["status"] != ref["status"]).mean()),
+                        "d_stop_abs_err_mean_m": float(dd.mean()),
+                        "d_stop_abs_err_max_m": float(dd.max()),
+                        "v_imp_abs_err_mean_mps": float(dv.mean()),
+                        "p_contact_err": row["p_contact"] - float((ref["status"] == 1).mean())})
+        res.append(row)
+        del O
+    return {"samples": N, "reference_dt_ms": 0.1, "precision": "fp32-compensated", "by_dt": res}
+
+
 def config(args, world):
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         "10 s horizon, lead at d0, per-axle caps, immediate trigger",
@@ -384,11 +437,13 @@ def main():
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
-    batched = sweep = None
+    batched = sweep = dts = None
     if not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
         sweep = sweep_run(aeb)
+        torch.cuda.empty_cache()
+        dts = dt_study(aeb, torch)
 
     if rank != 0:
         if dist:
@@ -429,6 +484,7 @@ def main():
         "serving": serving,
         "batched_grid": batched,
         "ttc_sweep": sweep,
+        "dt_study": dts,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
         "steps_per_rollout": steps_per_launch / N,
