@@ -52,6 +52,8 @@ class Model:
     cap_mode: int = CAP_PER_AXLE
     trigger: int = TRIGGER_IMMEDIATE
     lead: int = 1
+    lead_v0: float = 0.0     # moving lead: initial speed [m/s] (0: stationary)
+    lead_decel: float = 0.0  # moving lead: constant braking deceleration [m/s^2]
 
 
 @dataclass

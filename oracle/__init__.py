@@ -38,7 +38,8 @@ TRIGGER_IMMEDIATE, TRIGGER_TTC = 0, 1
 class _Model(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "g", "rho", "area", "h_cg", "wheelbase", "beta", "phi_f", "a_cmd", "dt", "t_max",
-        "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "pad_")]
+        "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "pad_")] + [
+        (n, C.c_double) for n in ("lead_v0", "lead_decel")]
 
 
 class _Dist(C.Structure):

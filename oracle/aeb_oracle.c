@@ -30,7 +30,8 @@
  *                      distributions, clamping and counter-layout invariants.
  *   om_rollout         pinned: closed forms (constant deceleration, constant
  *                      deceleration + quadratic drag, pure actuator lag, grade,
- *                      contact kinematics, TTC trigger step), RK4 order of
+ *                      contact kinematics, TTC trigger step, moving-lead contact
+ *                      and closing-speed trigger), RK4 order of
  *                      convergence, monotonicity sweeps, paper Table I / Sec. VI-C
  *                      statistics (statistical band).
  *   om_axle_cap        pinned: brute-force fixed-point iteration of the per-axle
@@ -65,8 +66,10 @@ typedef struct {
     double ttc_thr;    /* TTC trigger threshold [s]                           */
     int32_t cap_mode;  /* OM_CAP_*                                            */
     int32_t trigger;   /* OM_TRIGGER_*                                        */
-    int32_t lead;      /* 1: stationary lead vehicle at distance d0           */
+    int32_t lead;      /* 1: lead vehicle, initially at distance d0           */
     int32_t pad_;
+    double lead_v0;    /* initial speed of the lead [m/s] (0: stationary)     */
+    double lead_decel; /* constant braking deceleration of the lead [m/s^2]   */
 } om_model;
 
 /* Field order of a parameter set xi^(i) (structure-of-arrays columns). */
@@ -300,6 +303,32 @@ double om_axle_cap(const om_model *m, double mu, double gc, double D)
 }
 
 /*
+ * Moving lead (extension; Sec. VIII names other road users as future work).
+ * The lead starts d0 ahead of the ego car at speed lead_v0 and brakes at the
+ * constant deceleration lead_decel until it stops, then stays put:
+ *   x_L(t) = t (v_L0 - (b_L / 2) t)   for t < t_s = v_L0 / b_L,
+ *   x_L(t) = (v_L0 t_s) / 2           for t >= t_s,
+ *   v_L(t) = v_L0 - b_L t, then 0      (b_L = 0: t_s = infinity).
+ * This is exact (no integration); the gap is g = (d0 + x_L(t)) - x.
+ */
+static double lead_pos(const om_model *m, double t)
+{
+    const double vl = m->lead_v0, bl = m->lead_decel;
+    if (bl > 0.0) {
+        const double ts = vl / bl;
+        if (t >= ts) return 0.5 * (vl * ts);
+    }
+    return t * (vl - (0.5 * bl) * t);
+}
+
+static double lead_speed(const om_model *m, double t)
+{
+    const double vl = m->lead_v0, bl = m->lead_decel;
+    if (bl > 0.0 && t >= vl / bl) return 0.0;
+    return vl - bl * t;
+}
+
+/*
  * One rollout (Sec. IV-D): classic RK4 on Eq. 7-9 with the command held over
  * the step, until contact, stop (v <= 0, Sec. V-D) or the horizon.
  *
@@ -307,19 +336,25 @@ double om_axle_cap(const om_model *m, double mu, double gc, double D)
  * car coasts under drag and grade during the reaction delay).
  *   immediate trigger: n_b = n_delay (the paper's setting has no delay, n_b = 0)
  *   TTC trigger: at the start of step n, while not yet triggered, the measured
- *   gap (d0 - x_n) + noise is compared with ttc_thr * v_n; the first step n_t
- *   where gap <= thr * v sets n_b = n_t + n_delay.
+ *   gap ((d0 + x_L(t_n)) - x_n) + noise is compared with ttc_thr times the
+ *   closing speed v_n - v_L(t_n); the first step n_t where gap <= thr * closing
+ *   speed sets n_b = n_t + n_delay (stationary lead: x_L = v_L = 0, TTC = H0 / v
+ *   of Sec. VI-C).
  * Actuator (Eq. 6): tau == 0 means an instantaneous actuator (a == command at
  * every stage).
  *
  * Termination after step n -> n+1, in this order: contact if a lead is
- * present and x_{n+1} >= d0; stop if v_{n+1} <= 0; horizon if n+1 == N_max.
+ * present and the gap (d0 + x_L(t_{n+1})) - x_{n+1} <= 0 (stationary lead:
+ * x_{n+1} >= d0); stop if v_{n+1} <= 0; horizon if n+1 == N_max.
  * Outputs: n_onset = n_b once the command is issued (immediate trigger: always
  *   n_delay; TTC trigger: -1 if it never fires), x_raw = x_{n+1} (the paper's
  *   D_stop = x(t_stop), Eq. 3);
  *   stop:    s = v_n / (v_n - v_{n+1}),  x_ref = x_n + s (x_{n+1} - x_n)
- *   contact: s = (d0 - x_n) / (x_{n+1} - x_n), x_ref = d0,
+ *   contact, stationary lead: s = (d0 - x_n) / (x_{n+1} - x_n), x_ref = d0,
  *            v_imp = v_n + s (v_{n+1} - v_n)
+ *   contact, moving lead: with the gaps g_n, g_{n+1} and the closing speeds
+ *            c_n = v_n - v_L(t_n), c_{n+1}: s = g_n / (g_n - g_{n+1}),
+ *            x_ref = x_n + s (x_{n+1} - x_n), v_imp = c_n + s (c_{n+1} - c_n)
  *   t_end = (n + s) dt;  horizon: s = 1, x_ref = x_{n+1}.
  */
 static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, double *x_raw,
@@ -346,11 +381,20 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
     }
 
     int triggered = (m->trigger == OM_TRIGGER_IMMEDIATE);
+    const int moving = m->lead && m->lead_v0 > 0.0;
     int64_t n_b = c->n_delay;
     for (int64_t n = 0;; ++n) {
         if (!triggered) {
-            double gap_meas = (c->d0 - x) + c->noise;
-            if (gap_meas <= m->ttc_thr * v) {
+            double gap_meas, closing;
+            if (moving) {
+                const double t = (double)n * dt;
+                gap_meas = ((c->d0 + lead_pos(m, t)) - x) + c->noise;
+                closing = v - lead_speed(m, t);
+            } else {
+                gap_meas = (c->d0 - x) + c->noise;
+                closing = v;
+            }
+            if (gap_meas <= m->ttc_thr * closing) {
                 triggered = 1; n_b = n + c->n_delay;
                 *n_onset = (n_b > 2147483647) ? 2147483647 : (int32_t)n_b;
             }
@@ -382,7 +426,18 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
         double vn = v + h6 * (((kv1 + 2.0 * kv2) + 2.0 * kv3) + kv4);
         double an = (c->tau > 0.0) ? a + h6 * (((ka1 + 2.0 * ka2) + 2.0 * ka3) + ka4) : u;
 
-        if (m->lead && xn >= c->d0) {
+        if (moving) {
+            const double t0 = (double)n * dt, t1 = (double)(n + 1) * dt;
+            const double g1 = (c->d0 + lead_pos(m, t1)) - xn;
+            if (g1 <= 0.0) {
+                const double g0 = (c->d0 + lead_pos(m, t0)) - x;
+                const double c0 = v - lead_speed(m, t0), c1 = vn - lead_speed(m, t1);
+                double s = g0 / (g0 - g1);
+                *status = OM_CONTACT; *x_raw = xn; *x_ref = x + s * (xn - x);
+                *v_imp = c0 + s * (c1 - c0);
+                *t_end = ((double)n + s) * dt; *n_steps = (int32_t)(n + 1); return;
+            }
+        } else if (m->lead && xn >= c->d0) {
             double s = (c->d0 - x) / (xn - x);
             *status = OM_CONTACT; *x_raw = xn; *x_ref = c->d0;
             *v_imp = v + s * (vn - v);

@@ -405,3 +405,86 @@ def test_steps_to_reach(oracle_mod):
     for t in rng.uniform(0, 0.5, 500):
         n = oracle_mod.steps_to_reach(t, 1e-3)
         assert n * 1e-3 >= t and (n == 0 or (n - 1) * 1e-3 < t)
+
+
+# ---------------------------------------------------------------------------
+# Moving lead (extension): the lead starts d0 ahead at lead_v0 and brakes at
+# lead_decel until it stops.  Pins from closed-form kinematics of both cars.
+# ---------------------------------------------------------------------------
+
+def coasting_ego(v0, d0, t_max=10.0):
+    """Constant-speed ego car: no drag, flat road, brake onset beyond the horizon."""
+    return one([(v0, d0, 0.8, 0.0, 1500.0, 0.0, 0.0, 2.0 * t_max, 0.0)])
+
+
+def test_moving_lead_contact_while_lead_brakes(oracle_mod):
+    """Ego at 20 m/s, lead at 15 m/s braking at 3 m/s^2, 10 m ahead: the gap
+    10 - 5 t - 1.5 t^2 closes at t* = (-5 + sqrt(85)) / 3, before the lead stops."""
+    m = ai.Model(lead=1, lead_v0=15.0, lead_decel=3.0)
+    o = oracle_mod.rollout(m, coasting_ego(20.0, 10.0))
+    t = (-5.0 + math.sqrt(85.0)) / 3.0
+    assert o["status"][0] == 1
+    # the gap is quadratic in t; the linear root inside one step is off by < 1e-7 s
+    assert abs(o["t_end"][0] - t) < 1e-7
+    assert abs(o["x_ref"][0] - 20.0 * t) < 2e-6
+    assert abs(o["v_imp"][0] - (20.0 - (15.0 - 3.0 * t))) < 1e-6  # closing speed
+    assert o["n_steps"][0] == math.ceil(t / m.dt)
+
+
+def test_moving_lead_stops_before_contact(oracle_mod):
+    """Lead 10 m/s braking at 5 m/s^2 stops after 2 s and 10 m; the ego at
+    8 m/s from 20 m behind reaches it at t = 30 / 8 with closing speed 8."""
+    m = ai.Model(lead=1, lead_v0=10.0, lead_decel=5.0)
+    o = oracle_mod.rollout(m, coasting_ego(8.0, 20.0))
+    assert o["status"][0] == 1
+    assert abs(o["t_end"][0] - 30.0 / 8.0) < 1e-9
+    assert abs(o["x_ref"][0] - 30.0) < 1e-8
+    assert abs(o["v_imp"][0] - 8.0) < 1e-12
+
+
+def test_moving_lead_both_braking(oracle_mod):
+    """Both cars from 20 m/s, ego at a constant 6 m/s^2 (instantaneous
+    actuator, cap far above the demand), lead at 7 m/s^2, 3 m ahead: the gap
+    3 - t^2 / 2 closes at t = sqrt(6) (the lead stops at 20/7 s), closing
+    speed t, ego position 20 t - 3 t^2."""
+    m = ai.Model(lead=1, lead_v0=20.0, lead_decel=7.0, cap_mode=ai.CAP_LUMPED, a_cmd=-6.0)
+    o = oracle_mod.rollout(m, one([(20.0, 3.0, 5.0, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)]))
+    t = math.sqrt(6.0)
+    assert o["status"][0] == 1
+    assert abs(o["t_end"][0] - t) < 1e-7
+    assert abs(o["v_imp"][0] - t) < 1e-6
+    assert abs(o["x_ref"][0] - (20.0 * t - 3.0 * t * t)) < 2e-6
+    # same deceleration for both: the gap never closes; the ego stops at 20^2 / 12
+    m2 = ai.replace(m, lead_decel=6.0)
+    o2 = oracle_mod.rollout(m2, one([(20.0, 3.0, 5.0, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)]))
+    assert o2["status"][0] == 0
+    assert abs(o2["x_ref"][0] - 400.0 / 12.0) <= 6.0 * m.dt ** 2 / 8 + 1e-9
+
+
+def test_moving_lead_never_caught(oracle_mod):
+    """A lead faster than the coasting ego car is never reached."""
+    m = ai.Model(lead=1, lead_v0=25.0, lead_decel=0.0, t_max=5.0)
+    o = oracle_mod.rollout(m, coasting_ego(20.0, 1.0, t_max=5.0))
+    assert o["status"][0] == 2
+    assert abs(o["x_ref"][0] - 100.0) < 1e-9
+
+
+@pytest.mark.parametrize("thr", [1.5, 2.0, 3.2])
+def test_moving_lead_ttc_uses_closing_speed(oracle_mod, thr):
+    """TTC trigger against a lead at a constant 12 m/s: the ego car at 20 m/s
+    closes at 8 m/s, so the first step start with 60.0037 - 8 t <= 8 thr is
+    the trigger step (no delay: it is also the onset step)."""
+    m = ai.Model(lead=1, lead_v0=12.0, lead_decel=0.0, trigger=ai.TRIGGER_TTC, ttc_thr=thr)
+    p = one([(20.0, 60.0037, 0.8, 0.0, 1500.0, 0.0, 0.0, 0.0, 0.0)])
+    o = oracle_mod.rollout(m, p)
+    t = (60.0037 - 8.0 * thr) / 8.0
+    assert o["n_onset"][0] == math.ceil(t / m.dt)
+
+
+def test_stationary_lead_unchanged_by_lead_decel(oracle_mod):
+    """lead_v0 = 0 is the stationary lead whatever lead_decel says."""
+    p = ai.draw_params(ai.single_model(), ai.single_scenario(seed=61), 300)
+    a = oracle_mod.rollout(ai.single_model(), p)
+    b = oracle_mod.rollout(ai.replace(ai.single_model(), lead_decel=4.0), p)
+    for k in a:
+        assert np.array_equal(np.asarray(a[k]).view(np.uint8), np.asarray(b[k]).view(np.uint8)), k

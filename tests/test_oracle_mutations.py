@@ -23,7 +23,8 @@ MUTATIONS = [
     ("Eq. 5 sign", "c->cap = (mu * m->g) / (1.0 + mh);", "c->cap = (mu * m->g) / (1.0 - mh);"),
     ("no stop refinement", "double s = v / (v - vn);", "double s = 1.0;"),
     ("actuator stage", "ka2 = (u - a2) * c->it;", "ka2 = (u - a1) * c->it;"),
-    ("TTC threshold", "if (gap_meas <= m->ttc_thr * v)", "if (gap_meas < m->ttc_thr * v - 0.01)"),
+    ("TTC threshold", "if (gap_meas <= m->ttc_thr * closing)",
+     "if (gap_meas < m->ttc_thr * closing - 0.01)"),
     ("onset rounding", "c->n_delay = om_steps_to_reach(td, m->dt);",
      "c->n_delay = (int64_t)(td / m->dt);"),
     ("impact speed", "*v_imp = v + s * (vn - v);", "*v_imp = vn;"),
@@ -32,6 +33,12 @@ MUTATIONS = [
     ("contact test", "if (m->lead && xn >= c->d0) {", "if (m->lead && xn > c->d0 + 1e-3) {"),
     ("Philox key schedule", "if (round > 0) { k0 += W0; k1 += W1; }", "if (round > 0) { k0 += W0; }"),
     ("histogram origin", "double q = floor((x - lo) / w);", "double q = floor(x / w);"),
+    ("lead displacement sign", "const double g1 = (c->d0 + lead_pos(m, t1)) - xn;",
+     "const double g1 = (c->d0 - lead_pos(m, t1)) - xn;"),
+    ("TTC ego speed for closing speed", "closing = v - lead_speed(m, t);", "closing = v;"),
+    ("lead never stops", "if (t >= ts) return 0.5 * (vl * ts);",
+     "if (t >= ts + 1e9) return 0.5 * (vl * ts);"),
+    ("impact speed not relative", "c1 = vn - lead_speed(m, t1);", "c1 = vn;"),
 ]
 
 
