@@ -193,6 +193,18 @@ def ttc_scenarios(n: int = 64, seed: int = 4):
     return out
 
 
+def lead_braking_model(lead_v0: float = 50.0 / 3.6, lead_decel: float = 6.0,
+                       dt: float = 1e-3) -> Model:
+    """Moving-lead workload: a lead ahead at 50 km/h braking hard (6 m/s^2) at
+    t = 0, per-axle caps, immediate trigger."""
+    return Model(dt=dt, lead_v0=lead_v0, lead_decel=lead_decel)
+
+
+def lead_braking_scenario(seed: int = 0, scenario_id: int = 0) -> Scenario:
+    """The single-scenario distributions with a short headway, d0 ~ U(12, 40) m."""
+    return Scenario(d0=uniform(12.0, 40.0), seed=seed, scenario_id=scenario_id)
+
+
 def ttc_model(thr: float = 2.0, dt: float = 1e-3) -> Model:
     return Model(dt=dt, trigger=TRIGGER_TTC, ttc_thr=thr)
 

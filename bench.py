@@ -18,7 +18,8 @@ so no flush is needed between steps.
 Beside the headline the line carries the serving run (Poisson requests,
 latency percentiles), the scenario-grid batched run, the TTC-threshold sweep and
 a coarse-step study (the same samples at dt = 0.1 .. 20 ms: speed and the error
-against the 0.1 ms rollouts); `--no-extras` skips the last three.
+against the 0.1 ms rollouts) and a moving-lead run (a lead braking ahead);
+`--no-extras` skips the last four.
 
 `--impl reference` times the plain CPU oracle on a bounded sample of the same
 workload on the host cores (the CPU baseline), with the same metric.
@@ -292,6 +293,35 @@ def dt_study(aeb, torch):
     return {"samples": N, "reference_dt_ms": 0.1, "precision": "fp32-compensated", "by_dt": res}
 
 
+def moving_lead_run(aeb, torch):
+    """Moving lead: 1e7 samples with a short headway, d0 ~ U(12, 40) m, behind a
+    lead at 50 km/h that brakes at 6 m/s^2 from t = 0 (FP32-compensated, one
+    launch after a warm-up, device-resident parameters), with P(contact) and
+    the mean closing speed at impact."""
+    N = 10_000_000
+    m = ai.lead_braking_model()
+    p = aeb.aeb_sample_params(m, ai.lead_braking_scenario(seed=0), 0, N)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(N, which=("status", "x_ref", "v_imp", "n_steps"))
+    aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    S = aeb.alloc_stats()
+    aeb.aeb_reduce(O, N, aeb.hist_spec(), S)
+    st = aeb.stats_from_buffer(S)
+    del P, O
+    return {"samples": N, "ms": ms, "rollouts_per_s": N / (ms / 1e3),
+            "steps_per_rollout": st.steps / N, "p_contact": st.n_contact / st.n,
+            "mean_closing_speed_at_impact_mps": st.sum_v / max(st.n_contact, 1),
+            "lead": {"v0_mps": m.lead_v0, "decel_mps2": m.lead_decel},
+            "precision": "fp32-compensated"}
+
+
 def config(args, world):
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         "10 s horizon, lead at d0, per-axle caps, immediate trigger",
@@ -437,13 +467,15 @@ def main():
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
-    batched = sweep = dts = None
+    batched = sweep = dts = moving = None
     if not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
         sweep = sweep_run(aeb)
         torch.cuda.empty_cache()
         dts = dt_study(aeb, torch)
+        torch.cuda.empty_cache()
+        moving = moving_lead_run(aeb, torch)
 
     if rank != 0:
         if dist:
@@ -485,6 +517,7 @@ def main():
         "batched_grid": batched,
         "ttc_sweep": sweep,
         "dt_study": dts,
+        "moving_lead": moving,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
         "steps_per_rollout": steps_per_launch / N,

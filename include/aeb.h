@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define AEB_ABI_VERSION 1
+#define AEB_ABI_VERSION 2
 #define AEB_NFIELDS 10   /* columns of a parameter set, see aeb_params       */
 #define AEB_NBINS 4096   /* bins of each fixed histogram in aeb_stats         */
 
@@ -84,9 +84,18 @@ typedef struct aeb_model {
                           axle with weight transfer (extension)                  */
     int32_t trigger;   /* AEB_TRIGGER_IMMEDIATE: brake after the reaction delay;
                           AEB_TRIGGER_TTC: brake once the measured gap
-                          (d0 - x + noise) <= ttc_thr * v, then the delay        */
-    int32_t lead;      /* 1: stationary lead vehicle at d0 (contact ends a run)  */
+                          (gap + noise) <= ttc_thr * closing speed, then the
+                          delay (stationary lead: d0 - x + noise <= thr * v)    */
+    int32_t lead;      /* 1: lead vehicle, initially d0 ahead (contact ends a run) */
     int32_t reserved;  /* must be 0                                             */
+    /* Moving lead (extension; the paper's lead is stationary).  The lead starts
+       at lead_v0 and brakes at the constant lead_decel until it stops:
+       x_L(t) = t (v_L0 - lead_decel t / 2) up to t_s = v_L0 / lead_decel, then
+       constant; the gap is (d0 + x_L(t)) - x and the impact speed reported for
+       a contact is the closing speed v - v_L.  lead_v0 = 0: stationary lead.
+       Both finite and >= 0, else AEB_EINVAL.                                   */
+    double lead_v0;    /* initial speed of the lead [m/s]                       */
+    double lead_decel; /* braking deceleration of the lead [m/s^2]              */
 } aeb_model;
 
 /* ---- sampling description (Sec. IV-A, IV-C) ------------------------------ */

@@ -25,6 +25,7 @@ OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
 OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
               "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
               "n_onset": np.int32}
+ABI_VERSION = 2  # AEB_ABI_VERSION of include/aeb.h
 NBINS = 4096
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)
@@ -45,7 +46,8 @@ class AebError(RuntimeError):
 class Model(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "g", "rho", "area", "h_cg", "wheelbase", "beta", "phi_f", "a_cmd", "dt", "t_max",
-        "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "reserved")]
+        "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "reserved")] + [
+        (n, C.c_double) for n in ("lead_v0", "lead_decel")]
 
 
 class Dist(C.Structure):
@@ -172,7 +174,7 @@ def lib():
                        "aeb_serve_create", "aeb_serve_submit", "aeb_serve_poll",
                        "aeb_serve_cancel", "aeb_serve_counters_get"):
                 getattr(L, fn).restype = C.c_int32
-            if L.aeb_abi_version() != 1:
+            if L.aeb_abi_version() != ABI_VERSION:
                 raise ImportError("libaeb.so ABI version mismatch")
             _lib = L
     return _lib

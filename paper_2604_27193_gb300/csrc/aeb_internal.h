@@ -15,7 +15,11 @@ namespace aeb {
 // with n * dt >= t_max.
 struct ModelDev {
     double g, rho, area, hl, beta, phi_f, a_cmd, dt, h2, h6, ttc_thr;
+    // moving lead: initial speed, deceleration, stop time v/b (inf if b = 0),
+    // stop position (v t_s) / 2 (the same binary64 expressions as the oracle)
+    double lead_v0, lead_decel, lead_ts, lead_xs;
     int32_t n_max, cap_mode, trigger, lead;
+    int32_t lead_moving;  // lead && lead_v0 > 0
 };
 
 enum Field { kV0 = 0, kD0, kMu, kGs, kGc, kMass, kCd, kTau, kTdelay, kNoise };

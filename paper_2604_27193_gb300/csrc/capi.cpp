@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -51,7 +52,8 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
 {
     if (!m) return fail(AEB_EINVAL, "model is NULL");
     const double v[] = {m->g, m->rho, m->area, m->h_cg, m->wheelbase, m->beta,
-                        m->phi_f, m->a_cmd, m->dt, m->t_max, m->ttc_thr};
+                        m->phi_f, m->a_cmd, m->dt, m->t_max, m->ttc_thr,
+                        m->lead_v0, m->lead_decel};
     for (double x : v)
         if (!std::isfinite(x)) return fail(AEB_EINVAL, "model constant is not finite");
     if (!(m->dt > 0.0)) return fail(AEB_EINVAL, "model.dt must be > 0");
@@ -63,6 +65,8 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
         return fail(AEB_EINVAL, "model.trigger unknown");
     if (m->lead != 0 && m->lead != 1) return fail(AEB_EINVAL, "model.lead must be 0 or 1");
     if (m->reserved != 0) return fail(AEB_EINVAL, "model.reserved must be 0");
+    if (m->lead_v0 < 0.0 || m->lead_decel < 0.0)
+        return fail(AEB_EINVAL, "model.lead_v0 and model.lead_decel must be >= 0");
     const int64_t n_max = steps_to_reach_host(m->t_max, m->dt);
     if (n_max > 2147483646) return fail(AEB_EINVAL, "model.t_max / model.dt exceeds 2^31 - 2 steps");
     out->g = m->g;
@@ -80,6 +84,12 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
     out->cap_mode = m->cap_mode;
     out->trigger = m->trigger;
     out->lead = m->lead;
+    out->lead_v0 = m->lead_v0;
+    out->lead_decel = m->lead_decel;
+    out->lead_ts = (m->lead_decel > 0.0) ? m->lead_v0 / m->lead_decel
+                                         : std::numeric_limits<double>::infinity();
+    out->lead_xs = 0.5 * (m->lead_v0 * out->lead_ts);
+    out->lead_moving = (m->lead == 1 && m->lead_v0 > 0.0) ? 1 : 0;
     return AEB_OK;
 }
 

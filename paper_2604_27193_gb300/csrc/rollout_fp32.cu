@@ -78,7 +78,7 @@ constexpr int kThreads = 32 * kWarps;
 // p4 = -np4 and np1 = -1 when tau > 0, else 0, are derived where needed)
 enum {
     R_W0H, R_W0L, R_G0H, R_G0L, R_GS, R_S, R_NH2S, R_NH6S, R_F0, R_F1, R_R0, R_R1, R_MG,
-    R_NP2, R_NP3, R_NP4, R_NMP,
+    R_NP2, R_NP3, R_NP4, R_NMP, R_SIGMA,
     R_NF_BASE,                                   // float fields of every kernel
     R_NZ = R_NF_BASE, R_THRH, R_THRL, R_NF_TTC   // TTC trigger only
 };
@@ -87,8 +87,15 @@ template <bool TTC>
 __host__ __device__ constexpr int rec_floats() { return TTC ? R_NF_TTC : R_NF_BASE; }
 enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 
+// The lead vehicle, a template parameter of the kernel (so that a stationary
+// lead pays nothing for the moving one).
+enum { kNoLead = 0, kLeadStationary = 1, kLeadMoving = 2 };
+
 struct ModelF32 {
     float acmd;
+    // moving lead: step, initial speed, deceleration, half of it, stop time,
+    // stop position (binary32 copies of the model's values)
+    float dt, lv0, lb, lhb, lts, lxs;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -113,7 +120,7 @@ __device__ __forceinline__ float powi(float q)
 
 // Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
 // warp's shared slab.
-template <bool LEAD, bool TTC>
+template <int LEAD, bool TTC>
 __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P, uint64_t start,
                                           int cnt, double thr, int T, float *tf, int *ti)
 {
@@ -150,6 +157,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         tf[R_S * T + j] = sc;
         tf[R_NH2S * T + j] = __double2float_rn(-(sd * M.h2));
         tf[R_NH6S * T + j] = nh6s;
+        tf[R_SIGMA * T + j] = __double2float_rn(sigma);
         const double mu = f[kMu], mh = mu * M.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
             tf[R_F0 * T + j] = finf();
@@ -194,6 +202,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 // stride 32, to keep the step loop's register budget small.
 enum {
     L_F0, L_F1, L_R0, L_R1, L_MG, L_GS, L_U, L_S, L_ETHK, L_NP1, L_NP2, L_NP3, L_NP4,  // floats
+    L_SIGMA,
     L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                             // ints
     L_NW_BASE,
     L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NW_TTC  // TTC trigger only (floats)
@@ -201,7 +210,7 @@ enum {
 template <bool TTC>
 __host__ __device__ constexpr int cold_fields() { return TTC ? L_NW_TTC : L_NW_BASE; }
 
-template <bool LEAD, bool TTC>
+template <int LEAD, bool TTC>
 struct Lane32 {
     float vh, vl, gh, gl, e;      // state: scaled speed w = s v, scaled gap G = sigma (d0 - x),
                                   // actuator deviation a - u
@@ -325,10 +334,36 @@ struct Lane32 {
         gh = sg;
     }
 
-    // Whether the state (vh, vl1), (gh, gl1) has stopped or reached the lead.
-    __device__ __forceinline__ bool terminal(float vl1, float gl1) const
+    // Moving lead: the scaled distance sig x_L(m dt) the lead has covered by
+    // the start of step m (sig: the lane's gap scale), and its scaled speed
+    // sc v_L(m dt) (sc: the lane's speed scale), in binary32.
+    static __device__ __forceinline__ float lead_gap(const ModelF32 &F, int32_t m, float sig)
     {
-        return (LEAD && gh + gl1 <= 0.0f) || vh + vl1 <= 0.0f;
+        const float t = (float)m * F.dt;
+        const float x = (F.lb > 0.0f && t >= F.lts) ? F.lxs : t * fmaf(-F.lhb, t, F.lv0);
+        return sig * x;
+    }
+    static __device__ __forceinline__ float lead_speed(const ModelF32 &F, int32_t m, float sc)
+    {
+        const float t = (float)m * F.dt;
+        const float v = (F.lb > 0.0f && t >= F.lts) ? 0.0f : fmaf(-F.lb, t, F.lv0);
+        return sc * v;
+    }
+
+    // Whether the gap (gh, gl1) at the end of step n has closed.
+    __device__ __forceinline__ bool hits_lead(const ModelF32 &F, float gl1, float sig) const
+    {
+        if (!LEAD) return false;
+        float g = gh + gl1;
+        if (LEAD == kLeadMoving) g = g + lead_gap(F, n + 1, sig);
+        return g <= 0.0f;
+    }
+
+    // Whether the state (vh, vl1), (gh, gl1) has stopped or reached the lead.
+    __device__ __forceinline__ bool terminal(const ModelF32 &F, float vl1, float gl1,
+                                             float sig) const
+    {
+        return hits_lead(F, gl1, sig) || vh + vl1 <= 0.0f;
     }
 
     __device__ __forceinline__ void commit(float vl1, float gl1, float en)
@@ -342,11 +377,12 @@ struct Lane32 {
     // A checked step inside the current piece; true if the rollout ended
     // (contact or stop) in this step, which is then not committed (its
     // end-of-step low words are returned).
-    __device__ __forceinline__ bool step_fast(float &vl1, float &gl1)
+    __device__ __forceinline__ bool step_fast(const ModelF32 &F, float &vl1, float &gl1,
+                                              float sig)
     {
         float en;
         rk4_step<false>(vl1, gl1, en);
-        const bool ended = terminal(vl1, gl1);
+        const bool ended = terminal(F, vl1, gl1, sig);
         if (!ended) commit(vl1, gl1, en);
         return ended;
     }
@@ -406,7 +442,7 @@ struct Lane32 {
     // own length (the short-window version is a rolled loop, to keep the
     // kernel's code small).
     template <bool FULL>
-    __device__ __forceinline__ bool step_window(int len)
+    __device__ __forceinline__ bool step_window(const ModelF32 &F, int len)
     {
         const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
         if (FULL) {
@@ -418,7 +454,10 @@ struct Lane32 {
             for (int j = 0; j < len; ++j) step_unchecked();
         }
         normalize();
-        if ((LEAD && gh <= 0.0f) || vh <= 0.0f) {
+        bool hit = vh <= 0.0f;
+        if (LEAD == kLeadStationary) hit = hit || gh <= 0.0f;
+        if (LEAD == kLeadMoving) hit = hit || gh + lead_gap(F, n + len, cf(L_SIGMA)) <= 0.0f;
+        if (hit) {
             vh = vh0;
             vl = vl0;
             gh = gh0;
@@ -453,7 +492,7 @@ struct Lane32 {
         }
         float en;
         rk4_step<true>(vl1, gl1, en);
-        const bool ended = terminal(vl1, gl1) || n >= n_last;
+        const bool ended = terminal(F, vl1, gl1, cf(L_SIGMA)) || n >= n_last;
         if (!ended) {
             commit(vl1, gl1, en);
             normalize();
@@ -471,7 +510,8 @@ struct Lane32 {
     // and the margin falls by at most 6 W + thr' s dt max(0, -C) per step
     // (the gap by the stage-speed sum, the speed term by the speed gain); the
     // first L - 1 steps after this one cannot trigger while (L - 1) times that
-    // bound stays below the margin.
+    // bound stays below the margin.  With a moving lead the margin is
+    // (g + noise) - thr (v - v_L).
     __device__ __forceinline__ int ttc_check(const ModelF32 &F, int32_t n_last)
     {
         const float thr_h = cf(L_THRH);
@@ -479,7 +519,11 @@ struct Lane32 {
         const float pe = fmaf(thr_h, vh, -p);
         const float hi = gh - p;
         const float lo = (gl + cf(L_NZ)) - (pe + fmaf(thr_h, vl, cf(L_THRL) * vh));
-        const float m = hi + lo;
+        float m = hi + lo;
+        // moving lead: the gap grows by the lead's travel, the closing speed
+        // falls by its speed
+        if (LEAD == kLeadMoving)
+            m = m + fmaf(thr_h, lead_speed(F, n, cf(L_S)), lead_gap(F, n, cf(L_SIGMA)));
         if (m <= 0.0f) {
             trig = true;
             const long long nb = (long long)n + ci(L_NDELAY);
@@ -490,7 +534,9 @@ struct Lane32 {
         }
         const float sdt = -ndts, acc = fmaxf(0.0f, -C);
         const float W = fmaf((float)AEB_FP32_WINDOW * sdt, acc, vh + vl);
-        const float d = fmaf(6.0f, W, thr_h * sdt * acc) * 1.001f;
+        // (a braking lead's speed term falls by thr' s dt b_L per step more;
+        // its travel only widens the gap)
+        const float d = fmaf(6.0f, W, thr_h * sdt * (acc + F.lb)) * 1.001f;
         const float r = __fdividef(m, d) * 0.999f;
         return r >= (float)(AEB_FP32_WINDOW - 1) ? AEB_FP32_WINDOW : 1 + (int)r;
     }
@@ -537,6 +583,7 @@ struct Lane32 {
         set_cf(L_R1, tf[R_R1 * T + slot]);
         set_cf(L_MG, tf[R_MG * T + slot]);
         set_cf(L_S, tf[R_S * T + slot]);
+        set_cf(L_SIGMA, tf[R_SIGMA * T + slot]);
         set_ci(L_NDELAY, n_delay);
         set_ci(L_PIDXLO, (int)(uint32_t)pi);
         set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
@@ -566,7 +613,7 @@ struct Lane32 {
 // scales s (B_S) and -s h6 (B_NH6S) that undo the scaled units.
 enum {
     B_VH, B_VL, B_GH, B_GL, B_E, B_NH2S, B_NH6S, B_A1, B_A2, B_A3, B_A4, B_NMP,
-    B_C, B_S, B_NF
+    B_C, B_S, B_SIGMA, B_NF
 };
 enum { B_G1H = B_A1, B_G1L = B_A2, B_W1H = B_A3, B_W1L = B_A4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
@@ -585,7 +632,7 @@ __host__ __device__ constexpr size_t smem_per_block(int T)
 // For the warp's queued records, all 32 lanes at once: replay the windows that
 // contained an end one checked step at a time, then the binary64 refinement
 // of the last step (Sec. V-D termination; the refinement of the last step).
-template <bool LEAD, bool TTC>
+template <int LEAD, bool TTC>
 __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F,
                                             const ParamsDev &P, const OutDev &O,
                                             const float *bf, const int *bi, int count)
@@ -621,7 +668,8 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.n = bi[B_N * 32 + j];
             // ends within len steps: the window's last state is terminal
             float vl1, gl1;
-            for (int s = 1; !R.step_fast(vl1, gl1) && s < len; ++s) {
+            const float sig = bf[B_SIGMA * 32 + j];
+            for (int s = 1; !R.step_fast(F, vl1, gl1, sig) && s < len; ++s) {
             }
             g0h = R.gh;
             g0l = R.gl;
@@ -632,7 +680,7 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             w1h = R.vh;
             w1l = vl1;
             n1 = R.n + 1;
-            status = (LEAD && g1h + g1l <= 0.0f) ? AEB_CONTACT : AEB_STOP;
+            status = R.hits_lead(F, gl1, sig) ? AEB_CONTACT : AEB_STOP;
         } else {
             g0h = bf[B_GH * 32 + j];
             g0l = bf[B_GL * 32 + j];
@@ -653,7 +701,23 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
         const double w0 = ((double)w0h + (double)w0l) / sd;
         const double w1 = ((double)w1h + (double)w1l) / sd;
         const double n = (double)(n1 - 1);
-        if (status == AEB_CONTACT) {
+        if (status == AEB_CONTACT && LEAD == kLeadMoving) {
+            // gaps and closing speeds to the moving lead at both ends of the step
+            const double t0 = n * M.dt, t1 = (double)n1 * M.dt;
+            const double l0 = (M.lead_decel > 0.0 && t0 >= M.lead_ts)
+                                  ? M.lead_xs : t0 * (M.lead_v0 - (0.5 * M.lead_decel) * t0);
+            const double l1 = (M.lead_decel > 0.0 && t1 >= M.lead_ts)
+                                  ? M.lead_xs : t1 * (M.lead_v0 - (0.5 * M.lead_decel) * t1);
+            const double u0 = (M.lead_decel > 0.0 && t0 >= M.lead_ts) ? 0.0
+                                                                     : M.lead_v0 - M.lead_decel * t0;
+            const double u1 = (M.lead_decel > 0.0 && t1 >= M.lead_ts) ? 0.0
+                                                                     : M.lead_v0 - M.lead_decel * t1;
+            const double q0 = (d0 + l0) - x0, q1 = (d0 + l1) - x1;
+            const double s = q0 / (q0 - q1);
+            const double c0 = w0 - u0, c1 = w1 - u1;
+            store_out(O, i, AEB_CONTACT, x1, x0 + s * (x1 - x0), c0 + s * (c1 - c0),
+                      (n + s) * M.dt, n1, on);
+        } else if (status == AEB_CONTACT) {
             const double s = (d0 - x0) / (x1 - x0);
             store_out(O, i, AEB_CONTACT, x1, d0, w0 + s * (w1 - w0), (n + s) * M.dt, n1, on);
         } else if (status == AEB_STOP) {
@@ -669,7 +733,7 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
 // One warp walks tiles of kTile samples claimed from a global counter; see the
 // file comment.  No wait on other warps or on the host: the loop ends when the
 // tiles are used up and no lane holds a rollout.
-template <bool LEAD, bool TTC>
+template <int LEAD, bool TTC>
 __global__ void __launch_bounds__(kThreads, AEB_FP32_MIN_BLOCKS)
 k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
 {
@@ -753,9 +817,9 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         const bool win = active && !slow;
         bool replay = false;
         if (full) {
-            if (win) replay = L.template step_window<true>(len);
+            if (win) replay = L.template step_window<true>(F, len);
         } else {
-            if (win) replay = L.template step_window<false>(len);
+            if (win) replay = L.template step_window<false>(F, len);
         }
         ended = ended || replay;
         const unsigned endm = __ballot_sync(kFull, ended);
@@ -773,6 +837,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 bf[B_GL * 32 + j] = L.gl;
                 bf[B_NH6S * 32 + j] = L.nh6s;
                 bf[B_S * 32 + j] = L.cf(L_S);
+                bf[B_SIGMA * 32 + j] = L.cf(L_SIGMA);
                 bi[B_IDXLO * 32 + j] = L.ci(L_IDXLO);
                 bi[B_IDXHI * 32 + j] = L.ci(L_IDXHI);
                 bi[B_PIDXLO * 32 + j] = L.ci(L_PIDXLO);
@@ -794,7 +859,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     bf[B_G1L * 32 + j] = gl1;
                     bf[B_W1H * 32 + j] = L.vh;
                     bf[B_W1L * 32 + j] = vl1;
-                    bi[B_STATUS * 32 + j] = (LEAD && L.gh + gl1 <= 0.0f)
+                    bi[B_STATUS * 32 + j] = L.hits_lead(F, gl1, L.cf(L_SIGMA))
                                                 ? AEB_CONTACT
                                                 : (L.vh + vl1 <= 0.0f ? AEB_STOP : AEB_HORIZON);
                     bi[B_N * 32 + j] = L.n + 1;
@@ -811,10 +876,16 @@ ModelF32 to_f32(const ModelDev &m)
 {
     ModelF32 f;
     f.acmd = (float)m.a_cmd;
+    f.dt = (float)m.dt;
+    f.lv0 = (float)m.lead_v0;
+    f.lb = (float)m.lead_decel;
+    f.lhb = (float)(0.5 * m.lead_decel);
+    f.lts = (float)m.lead_ts;
+    f.lxs = (float)m.lead_xs;
     return f;
 }
 
-template <bool LEAD, bool TTC>
+template <int LEAD, bool TTC>
 cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, const WorkDev &w,
                      const LaunchCfg &cfg, cudaStream_t s)
 {
@@ -852,10 +923,12 @@ cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, con
 cudaError_t launch_rollout_fp32(const ModelDev &m, const ParamsDev &p, const OutDev &o,
                                 const WorkDev &w, const LaunchCfg &cfg, cudaStream_t s)
 {
-    const bool lead = m.lead != 0, ttc = m.trigger == AEB_TRIGGER_TTC;
-    if (lead) return ttc ? launch_t<true, true>(m, p, o, w, cfg, s)
-                         : launch_t<true, false>(m, p, o, w, cfg, s);
-    return ttc ? launch_t<false, true>(m, p, o, w, cfg, s) : launch_t<false, false>(m, p, o, w, cfg, s);
+    const bool ttc = m.trigger == AEB_TRIGGER_TTC;
+    if (m.lead_moving) return ttc ? launch_t<kLeadMoving, true>(m, p, o, w, cfg, s)
+                                  : launch_t<kLeadMoving, false>(m, p, o, w, cfg, s);
+    if (m.lead) return ttc ? launch_t<kLeadStationary, true>(m, p, o, w, cfg, s)
+                           : launch_t<kLeadStationary, false>(m, p, o, w, cfg, s);
+    return ttc ? launch_t<kNoLead, true>(m, p, o, w, cfg, s) : launch_t<kNoLead, false>(m, p, o, w, cfg, s);
 }
 
 }  // namespace aeb

@@ -33,6 +33,20 @@ struct NoExtra {};
 
 __device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000ll); }
 
+// Moving lead (extension): the lead brakes from lead_v0 at lead_decel until it
+// stops (stop time lead_ts, stop position lead_xs), in closed form.
+__device__ __forceinline__ double lead_pos(const ModelDev &M, double t)
+{
+    if (M.lead_decel > 0.0 && t >= M.lead_ts) return M.lead_xs;
+    return t * (M.lead_v0 - (0.5 * M.lead_decel) * t);
+}
+
+__device__ __forceinline__ double lead_speed(const ModelDev &M, double t)
+{
+    if (M.lead_decel > 0.0 && t >= M.lead_ts) return 0.0;
+    return M.lead_v0 - M.lead_decel * t;
+}
+
 template <int CAP, bool LEAD, bool TTC>
 struct Lane64 {
     double x, v, a;
@@ -179,8 +193,16 @@ struct Lane64 {
     {
         const double dt = M.dt, h2 = M.h2, h6 = M.h6;
         if (TTC && !trig) {
-            double gap_meas = (d0 - x) + noise;
-            if (gap_meas <= thr * v) {
+            double gap_meas, closing;
+            if (M.lead_moving) {  // gap and closing speed to the moving lead
+                const double t = (double)n * dt;
+                gap_meas = ((d0 + lead_pos(M, t)) - x) + noise;
+                closing = v - lead_speed(M, t);
+            } else {
+                gap_meas = (d0 - x) + noise;
+                closing = v;
+            }
+            if (gap_meas <= thr * closing) {
                 trig = true;
                 long long nb = (long long)n + n_delay;
                 n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
@@ -232,7 +254,18 @@ struct Lane64 {
         const double vn = v + h6 * (((kv1 + 2.0 * kv2) + 2.0 * kv3) + kv4);
         const double an = lagged ? a + h6 * (((ka1 + 2.0 * ka2) + 2.0 * ka3) + ka4) : u;
 
-        if (LEAD && xn >= d0) {
+        if (LEAD && M.lead_moving) {
+            const double t0 = (double)n * dt, t1 = (double)(n + 1) * dt;
+            const double g1 = (d0 + lead_pos(M, t1)) - xn;
+            if (g1 <= 0.0) {
+                const double g0 = (d0 + lead_pos(M, t0)) - x;
+                const double c0 = v - lead_speed(M, t0), c1 = vn - lead_speed(M, t1);
+                const double s = g0 / (g0 - g1);
+                store_out(O, i, AEB_CONTACT, xn, x + s * (xn - x), c0 + s * (c1 - c0),
+                          ((double)n + s) * dt, n + 1, onset());
+                return true;
+            }
+        } else if (LEAD && xn >= d0) {
             const double s = (d0 - x) / (xn - x);
             store_out(O, i, AEB_CONTACT, xn, d0, v + s * (vn - v), ((double)n + s) * dt, n + 1,
                       onset());

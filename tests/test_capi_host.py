@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(aeb):
     L = C.CDLL(aeb._build.LIB)
     for n in names:
         assert hasattr(L, n), n
-    assert aeb.lib().aeb_abi_version() == 1
+    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 2
 
 
 def test_struct_layouts_match_header(aeb, tmp_path):
@@ -127,7 +127,8 @@ def test_invalid_arguments_rejected_on_host(aeb):
     bad = []
     for field, val in (("dt", 0.0), ("dt", float("nan")), ("t_max", -1.0), ("wheelbase", 0.0),
                        ("cap_mode", 7), ("trigger", 3), ("lead", 2), ("reserved", 1),
-                       ("g", float("inf"))):
+                       ("g", float("inf")), ("lead_v0", -1.0), ("lead_decel", -0.5),
+                       ("lead_v0", float("nan"))):
         mm = aeb.model(ai.single_model())
         setattr(mm, field, val)
         bad.append(mm)

@@ -77,6 +77,13 @@ FP64_CASES = {
     "coarse_dt_20ms": (ai.single_model(dt=0.02), ai.single_scenario(seed=6), 3_000),
     "fine_dt_0.1ms": (ai.single_model(dt=1e-4), ai.single_scenario(seed=7), 300),
     "short_horizon": (ai.replace(ai.single_model(), t_max=1.5), ai.single_scenario(seed=8), 2_000),
+    "moving_lead_braking": (ai.lead_braking_model(), ai.lead_braking_scenario(seed=9), 5_000),
+    "moving_lead_constant": (ai.lead_braking_model(lead_v0=10.0, lead_decel=0.0),
+                             ai.lead_braking_scenario(seed=15), 3_000),
+    "moving_lead_ttc": (ai.replace(ai.lead_braking_model(lead_decel=4.0), trigger=ai.TRIGGER_TTC,
+                                   ttc_thr=3.0), ai.lead_braking_scenario(seed=16), 3_000),
+    "moving_lead_lumped_20ms": (ai.replace(ai.lead_braking_model(dt=0.02), cap_mode=ai.CAP_LUMPED),
+                                ai.lead_braking_scenario(seed=17), 3_000),
 }
 
 
@@ -161,9 +168,21 @@ def fp32_report(m, got, exp):
     return rep
 
 
-def with_gap(out, p, lead):
+def lead_pos(m, t):
+    """Closed-form position of the braking lead at times t (numpy)."""
+    if m.lead_decel > 0.0:
+        ts = m.lead_v0 / m.lead_decel
+        return np.where(t >= ts, 0.5 * m.lead_v0 * ts, t * (m.lead_v0 - 0.5 * m.lead_decel * t))
+    return t * m.lead_v0
+
+
+def with_gap(out, p, m):
+    """The gap to the lead where each rollout ended (inf without a lead)."""
     out = dict(out)
-    out["gap"] = (p["d0"] - out["x_ref"]) if lead else np.full(len(out["x_ref"]), np.inf)
+    if not m.lead:
+        out["gap"] = np.full(len(out["x_ref"]), np.inf)
+    else:
+        out["gap"] = (p["d0"] + lead_pos(m, out["t_end"])) - out["x_ref"]
     return out
 
 
@@ -173,6 +192,11 @@ FP32_CASES = {
     "single_scenario_dt_0.1ms": (ai.single_model(dt=1e-4), ai.single_scenario(seed=12), 400),
     "ttc_2s": (ai.ttc_model(thr=2.0), ai.single_scenario(seed=13), 10_000),
     "grid_scenario": (ai.single_model(), ai.grid_scenarios()[1234][0], 5_000),
+    "moving_lead_braking": (ai.lead_braking_model(), ai.lead_braking_scenario(seed=18), 20_000),
+    "moving_lead_constant": (ai.lead_braking_model(lead_v0=10.0, lead_decel=0.0),
+                             ai.lead_braking_scenario(seed=19), 10_000),
+    "moving_lead_ttc": (ai.replace(ai.lead_braking_model(lead_decel=4.0), trigger=ai.TRIGGER_TTC,
+                                   ttc_thr=3.0), ai.lead_braking_scenario(seed=20), 10_000),
 }
 
 
@@ -180,8 +204,8 @@ FP32_CASES = {
 def test_fp32_comp_within_tolerance(aeb, oracle_mod, name):
     m, sc, n = FP32_CASES[name]
     p = ai.draw_params(m, sc, n)
-    exp = with_gap(oracle_mod.rollout(m, p, threads=8), p, m.lead)
-    got = with_gap(gpu_rollout(aeb, m, p, aeb.FP32_COMP), p, m.lead)
+    exp = with_gap(oracle_mod.rollout(m, p, threads=8), p, m)
+    got = with_gap(gpu_rollout(aeb, m, p, aeb.FP32_COMP), p, m)
     rep = fp32_report(m, got, exp)
     print(name, rep)
     if m.trigger == ai.TRIGGER_TTC:
@@ -295,6 +319,6 @@ def test_full_size_sampled(aeb, oracle_mod):
     rng = np.random.default_rng(0)
     idx = np.unique(np.concatenate([rng.integers(0, n, 3000), [0, 1, n - 2, n - 1]]))
     sub = {f: p[f][idx] for f in ai.FIELDS}
-    exp = with_gap(oracle_mod.rollout(m, sub, threads=8), sub, 1)
-    g = with_gap({k: v[idx] for k, v in got.items()}, sub, 1)
+    exp = with_gap(oracle_mod.rollout(m, sub, threads=8), sub, m)
+    g = with_gap({k: v[idx] for k, v in got.items()}, sub, m)
     fp32_report(m, g, exp)
