@@ -54,6 +54,10 @@ class Model:
     lead: int = 1
     lead_v0: float = 0.0     # moving lead: initial speed [m/s] (0: stationary)
     lead_decel: float = 0.0  # moving lead: constant braking deceleration [m/s^2]
+    perc_sigma: float = 0.0    # per-step perception noise scale [m] (TTC trigger)
+    perc_drop: float = 0.0     # probability that a step's reading is missing
+    perc_latency: float = 0.0  # age of a reading when it is used [s]
+    perc_seed: int = 0         # key of the per-step perception stream
 
 
 @dataclass

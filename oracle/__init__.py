@@ -39,7 +39,8 @@ class _Model(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "g", "rho", "area", "h_cg", "wheelbase", "beta", "phi_f", "a_cmd", "dt", "t_max",
         "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "pad_")] + [
-        (n, C.c_double) for n in ("lead_v0", "lead_decel")]
+        (n, C.c_double) for n in ("lead_v0", "lead_decel", "perc_sigma", "perc_drop",
+                                  "perc_latency")] + [("perc_seed", C.c_uint64)]
 
 
 class _Dist(C.Structure):
@@ -98,6 +99,8 @@ def lib():
             L.om_axle_cap.restype = C.c_double
             L.om_steps_to_reach.argtypes = [C.c_double, C.c_double]
             L.om_steps_to_reach.restype = C.c_int64
+            L.om_perception.argtypes = [P(_Model), C.c_uint64, C.c_int64, P(C.c_double)]
+            L.om_perception.restype = C.c_int
             _lib = L
     return _lib
 
@@ -205,6 +208,15 @@ def axle_cap(model, mu: float, gc: float, D: float) -> float:
 
 def steps_to_reach(t: float, dt: float) -> int:
     return int(lib().om_steps_to_reach(t, dt))
+
+
+def perception(model, row: int, k: int):
+    """(present, noise) of the per-step perception reading of step k for
+    parameter row `row`."""
+    m = _model(model)
+    x = C.c_double(0.0)
+    present = lib().om_perception(C.byref(m), row, k, C.byref(x))
+    return bool(present), x.value
 
 
 # --------------------------------------------------------------------------

@@ -34,6 +34,9 @@
  *                      and closing-speed trigger), RK4 order of
  *                      convergence, monotonicity sweeps, paper Table I / Sec. VI-C
  *                      statistics (statistical band).
+ *   om_perception      pinned: numpy's Philox-4x64-10 per reading, the exact
+ *                      Irwin-Hall CDF, dropout frequency; the trigger step of
+ *                      coasting cars against a brute-force search, latency shift.
  *   om_axle_cap        pinned: brute-force fixed-point iteration of the per-axle
  *                      force balance.
  *   om_reduce          pinned: numpy / math.fsum brute force over the outputs.
@@ -70,6 +73,10 @@ typedef struct {
     int32_t pad_;
     double lead_v0;    /* initial speed of the lead [m/s] (0: stationary)     */
     double lead_decel; /* constant braking deceleration of the lead [m/s^2]   */
+    double perc_sigma;   /* per-step perception noise scale [m] (TTC trigger)  */
+    double perc_drop;    /* probability that a step's reading is missing        */
+    double perc_latency; /* age of a reading when it is used [s]                */
+    uint64_t perc_seed;  /* key of the per-step perception stream               */
 } om_model;
 
 /* Field order of a parameter set xi^(i) (structure-of-arrays columns). */
@@ -329,6 +336,39 @@ static double lead_speed(const om_model *m, double t)
 }
 
 /*
+ * Per-step perception (extension; Sec. VIII names noise, latency and dropout
+ * of the perception chain as future work), TTC trigger only.  The reading
+ * taken at step k = n + L describes the state of step n (L = smallest integer
+ * with L dt >= perc_latency).  Its words are Philox-4x64-10 of counter
+ * (sample row, k, 0, 0) under key (perc_seed, "PERCEPT1"); with the uniforms
+ * u_j = (w_j >> 11) 2^-53, the reading is missing if u_4 < perc_drop, else its
+ * noise is perc_sigma * 2 ((u_1 + u_2) + u_3 - 1.5): zero mean, unit variance
+ * (Irwin-Hall of three uniforms, bounded by +-3 perc_sigma, close to normal),
+ * so no transcendental function enters the trigger decision.
+ */
+static const uint64_t PERC_KEY1 = 0x5045524345505431ULL; /* "PERCEPT1" */
+
+/* Returns 0 if the reading of step k is missing, else 1 and its noise. */
+static int perception(const om_model *m, uint64_t row, int64_t k, double *noise)
+{
+    const double two_m53 = 1.0 / 9007199254740992.0; /* 2^-53 */
+    uint64_t ctr[4] = {row, (uint64_t)k, 0, 0}, key[2] = {m->perc_seed, PERC_KEY1}, w[4];
+    om_philox4x64_10(ctr, key, w);
+    double u1 = (double)(w[0] >> 11) * two_m53, u2 = (double)(w[1] >> 11) * two_m53;
+    double u3 = (double)(w[2] >> 11) * two_m53, u4 = (double)(w[3] >> 11) * two_m53;
+    if (u4 < m->perc_drop) return 0;
+    *noise = m->perc_sigma * (2.0 * (((u1 + u2) + u3) - 1.5));
+    return 1;
+}
+
+/* Exposed for the perception pins: 1 and the noise, or 0 if missing. */
+int om_perception(const om_model *m, uint64_t row, int64_t k, double *noise)
+{
+    *noise = 0.0;
+    return perception(m, row, k, noise);
+}
+
+/*
  * One rollout (Sec. IV-D): classic RK4 on Eq. 7-9 with the command held over
  * the step, until contact, stop (v <= 0, Sec. V-D) or the horizon.
  *
@@ -339,7 +379,9 @@ static double lead_speed(const om_model *m, double t)
  *   gap ((d0 + x_L(t_n)) - x_n) + noise is compared with ttc_thr times the
  *   closing speed v_n - v_L(t_n); the first step n_t where gap <= thr * closing
  *   speed sets n_b = n_t + n_delay (stationary lead: x_L = v_L = 0, TTC = H0 / v
- *   of Sec. VI-C).
+ *   of Sec. VI-C).  With per-step perception the test at step n uses the
+ *   reading of step n + L (plus its noise; none if it is missing) and then
+ *   n_b = (n_t + L) + n_delay.
  * Actuator (Eq. 6): tau == 0 means an instantaneous actuator (a == command at
  * every stage).
  *
@@ -357,9 +399,9 @@ static double lead_speed(const om_model *m, double t)
  *            x_ref = x_n + s (x_{n+1} - x_n), v_imp = c_n + s (c_{n+1} - c_n)
  *   t_end = (n + s) dt;  horizon: s = 1, x_ref = x_{n+1}.
  */
-static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, double *x_raw,
-                        double *x_ref, double *v_imp, double *t_end, int32_t *n_steps,
-                        int32_t *n_onset)
+static void rollout_one(const om_model *m, const om_consts *c, uint64_t row, uint8_t *status,
+                        double *x_raw, double *x_ref, double *v_imp, double *t_end,
+                        int32_t *n_steps, int32_t *n_onset)
 {
     const double dt = m->dt;
     const double h2 = 0.5 * dt;
@@ -382,6 +424,8 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
 
     int triggered = (m->trigger == OM_TRIGGER_IMMEDIATE);
     const int moving = m->lead && m->lead_v0 > 0.0;
+    const int perc = m->perc_sigma > 0.0 || m->perc_drop > 0.0 || m->perc_latency > 0.0;
+    const int64_t lat = perc ? om_steps_to_reach(m->perc_latency, dt) : 0;
     int64_t n_b = c->n_delay;
     for (int64_t n = 0;; ++n) {
         if (!triggered) {
@@ -394,8 +438,14 @@ static void rollout_one(const om_model *m, const om_consts *c, uint8_t *status, 
                 gap_meas = (c->d0 - x) + c->noise;
                 closing = v;
             }
-            if (gap_meas <= m->ttc_thr * closing) {
-                triggered = 1; n_b = n + c->n_delay;
+            int reading = 1;
+            if (perc) {
+                double pn = 0.0;
+                reading = perception(m, row, n + lat, &pn);
+                gap_meas = gap_meas + pn;
+            }
+            if (reading && gap_meas <= m->ttc_thr * closing) {
+                triggered = 1; n_b = (n + lat) + c->n_delay;
                 *n_onset = (n_b > 2147483647) ? 2147483647 : (int32_t)n_b;
             }
         }
@@ -467,8 +517,8 @@ int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t
             t_end[i] = NAN; n_steps[i] = 0; n_onset[i] = -1;
             continue;
         }
-        rollout_one(m, &c, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i], &n_steps[i],
-                    &n_onset[i]);
+        rollout_one(m, &c, i, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i],
+                    &n_steps[i], &n_onset[i]);
     }
     return 0;
 }

@@ -39,6 +39,12 @@ MUTATIONS = [
     ("lead never stops", "if (t >= ts) return 0.5 * (vl * ts);",
      "if (t >= ts + 1e9) return 0.5 * (vl * ts);"),
     ("impact speed not relative", "c1 = vn - lead_speed(m, t1);", "c1 = vn;"),
+    ("perception word", "double u3 = (double)(w[2] >> 11) * two_m53",
+     "double u3 = (double)(w[1] >> 11) * two_m53"),
+    ("dropout sense", "if (u4 < m->perc_drop) return 0;", "if (u4 > m->perc_drop) return 0;"),
+    ("latency onset", "n_b = (n + lat) + c->n_delay;", "n_b = n + c->n_delay;"),
+    ("reading index", "reading = perception(m, row, n + lat, &pn);",
+     "reading = perception(m, row, n, &pn);"),
 ]
 
 
@@ -53,7 +59,8 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
                     str(so), str(mutated), "-lm"], check=True)
     env = dict(os.environ, AEB_ORACLE_SO=str(so))
     tests = [os.path.join(ROOT, "tests", f) for f in
-             ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py")]
+             ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py",
+              "test_oracle_perception.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         *tests], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"mutation '{name}' survived:\n{r.stdout[-2000:]}"
