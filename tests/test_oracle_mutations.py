@@ -23,8 +23,8 @@ MUTATIONS = [
     ("Eq. 5 sign", "c->cap = (mu * m->g) / (1.0 + mh);", "c->cap = (mu * m->g) / (1.0 - mh);"),
     ("no stop refinement", "double s = v / (v - vn);", "double s = 1.0;"),
     ("actuator stage", "ka2 = (u - a2) * c->it;", "ka2 = (u - a1) * c->it;"),
-    ("TTC threshold", "if (gap_meas <= m->ttc_thr * closing)",
-     "if (gap_meas < m->ttc_thr * closing - 0.01)"),
+    ("TTC threshold", "if (reading && gap_meas <= m->ttc_thr * closing)",
+     "if (reading && gap_meas < m->ttc_thr * closing - 0.01)"),
     ("onset rounding", "c->n_delay = om_steps_to_reach(td, m->dt);",
      "c->n_delay = (int64_t)(td / m->dt);"),
     ("impact speed", "*v_imp = v + s * (vn - v);", "*v_imp = vn;"),
