@@ -87,7 +87,7 @@ def lib():
             L.om_philox4x64_10.argtypes = [P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
             L.om_sample.argtypes = [P(_Model), P(_Scenario), C.c_uint64, C.c_uint64,
                                     P(P(C.c_double))]
-            L.om_rollout.argtypes = [P(_Model), P(P(C.c_double)), C.c_uint64,
+            L.om_rollout.argtypes = [P(_Model), P(P(C.c_double)), C.c_uint64, C.c_uint64,
                                      P(C.c_uint8), P(C.c_double), P(C.c_double),
                                      P(C.c_double), P(C.c_double), P(C.c_int32),
                                      P(C.c_int32)]
@@ -165,7 +165,8 @@ def sample(model, scenario, first: int, n: int) -> dict:
 
 def rollout(model, params: dict, threads: int = 1) -> dict:
     """Run every sample of ``params``; ``threads`` > 1 splits the samples into
-    contiguous blocks handled by the same single-sample code in parallel."""
+    contiguous blocks handled by the same single-sample code in parallel (each
+    sample keeps its row index, which keys its perception readings)."""
     n = len(params["v0"])
     out = {
         "status": np.empty(n, dtype=np.uint8),
@@ -182,7 +183,7 @@ def rollout(model, params: dict, threads: int = 1) -> dict:
     def run(lo: int, hi: int):
         arr, keep = _cols_array(params, lo)
         P = C.POINTER
-        L.om_rollout(C.byref(m), arr, hi - lo,
+        L.om_rollout(C.byref(m), arr, lo, hi - lo,
                      C.cast(C.c_void_p(out["status"].ctypes.data + lo), P(C.c_uint8)),
                      *[C.cast(C.c_void_p(out[k].ctypes.data + 8 * lo), P(C.c_double))
                        for k in ("x_raw", "x_ref", "v_imp", "t_end")],

@@ -506,7 +506,7 @@ static void rollout_one(const om_model *m, const om_consts *c, uint64_t row, uin
     }
 }
 
-int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t n,
+int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t row0, uint64_t n,
                uint8_t *status, double *x_raw, double *x_ref, double *v_imp, double *t_end,
                int32_t *n_steps, int32_t *n_onset)
 {
@@ -517,7 +517,7 @@ int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t
             t_end[i] = NAN; n_steps[i] = 0; n_onset[i] = -1;
             continue;
         }
-        rollout_one(m, &c, i, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i],
+        rollout_one(m, &c, row0 + i, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i],
                     &n_steps[i], &n_onset[i]);
     }
     return 0;

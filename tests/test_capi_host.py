@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(aeb):
     L = C.CDLL(aeb._build.LIB)
     for n in names:
         assert hasattr(L, n), n
-    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 2
+    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 3
 
 
 def test_struct_layouts_match_header(aeb, tmp_path):
@@ -128,7 +128,8 @@ def test_invalid_arguments_rejected_on_host(aeb):
     for field, val in (("dt", 0.0), ("dt", float("nan")), ("t_max", -1.0), ("wheelbase", 0.0),
                        ("cap_mode", 7), ("trigger", 3), ("lead", 2), ("reserved", 1),
                        ("g", float("inf")), ("lead_v0", -1.0), ("lead_decel", -0.5),
-                       ("lead_v0", float("nan"))):
+                       ("lead_v0", float("nan")), ("perc_sigma", -0.1), ("perc_drop", 1.5),
+                       ("perc_latency", -1.0), ("perc_sigma", float("inf"))):
         mm = aeb.model(ai.single_model())
         setattr(mm, field, val)
         bad.append(mm)

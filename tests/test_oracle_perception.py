@@ -116,3 +116,15 @@ def test_no_perception_is_the_plain_trigger(oracle_mod):
     b = oracle_mod.rollout(ai.replace(m, perc_seed=12345), p)
     for k in a:
         assert np.array_equal(np.asarray(a[k]).view(np.uint8), np.asarray(b[k]).view(np.uint8)), k
+
+
+def test_readings_follow_the_row_not_the_thread_split(oracle_mod):
+    """A sample's readings are keyed by its parameter row, so splitting the
+    rows over threads changes nothing."""
+    m = ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2, perc_latency=0.05,
+                   perc_seed=11)
+    p = ai.draw_params(m, ai.single_scenario(seed=21), 999)
+    a = oracle_mod.rollout(m, p, threads=1)
+    b = oracle_mod.rollout(m, p, threads=7)
+    for k in a:
+        assert np.array_equal(np.asarray(a[k]).view(np.uint8), np.asarray(b[k]).view(np.uint8)), k

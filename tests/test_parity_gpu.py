@@ -84,6 +84,12 @@ FP64_CASES = {
                                    ttc_thr=3.0), ai.lead_braking_scenario(seed=16), 3_000),
     "moving_lead_lumped_20ms": (ai.replace(ai.lead_braking_model(dt=0.02), cap_mode=ai.CAP_LUMPED),
                                 ai.lead_braking_scenario(seed=17), 3_000),
+    "ttc_perception": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2,
+                                  perc_latency=0.05, perc_seed=11), ai.single_scenario(seed=21), 3_000),
+    "moving_lead_ttc_perception": (ai.replace(ai.lead_braking_model(lead_decel=4.0),
+                                              trigger=ai.TRIGGER_TTC, ttc_thr=3.0, perc_sigma=1.5,
+                                              perc_drop=0.4, perc_latency=0.0123, perc_seed=12),
+                                   ai.lead_braking_scenario(seed=22), 3_000),
 }
 
 
@@ -197,6 +203,8 @@ FP32_CASES = {
                              ai.lead_braking_scenario(seed=19), 10_000),
     "moving_lead_ttc": (ai.replace(ai.lead_braking_model(lead_decel=4.0), trigger=ai.TRIGGER_TTC,
                                    ttc_thr=3.0), ai.lead_braking_scenario(seed=20), 10_000),
+    "ttc_perception": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2,
+                                  perc_latency=0.05, perc_seed=13), ai.single_scenario(seed=23), 10_000),
 }
 
 
