@@ -18,8 +18,8 @@ so no flush is needed between steps.
 Beside the headline the line carries the serving run (Poisson requests,
 latency percentiles), the scenario-grid batched run, the TTC-threshold sweep and
 a coarse-step study (the same samples at dt = 0.1 .. 20 ms: speed and the error
-against the 0.1 ms rollouts) and a moving-lead run (a lead braking ahead);
-`--no-extras` skips the last four.
+against the 0.1 ms rollouts), a moving-lead run (a lead braking ahead) and a
+TTC run with noisy, late and missing readings; `--no-extras` skips the last five.
 
 `--impl reference` times the plain CPU oracle on a bounded sample of the same
 workload on the host cores (the CPU baseline), with the same metric.
@@ -322,6 +322,39 @@ def moving_lead_run(aeb, torch):
             "precision": "fp32-compensated"}
 
 
+def perception_run(aeb, torch):
+    """Per-step perception of the TTC trigger: 2e6 samples of the single-scenario
+    distributions, TTC threshold 2 s, with readings carrying 1 m of noise,
+    missing with probability 0.2 and 50 ms old, against the plain trigger on the
+    same samples (FP32-compensated; time per launch and P(contact))."""
+    N = 2_000_000
+    base = ai.ttc_model(thr=2.0)
+    p = aeb.aeb_sample_params(base, ai.single_scenario(seed=0), 0, N)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(N, which=("status", "x_ref", "v_imp", "n_steps"))
+    out = {}
+    for name, m in (("plain", base),
+                    ("perception", ai.replace(base, perc_sigma=1.0, perc_drop=0.2,
+                                              perc_latency=0.05, perc_seed=1))):
+        aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        S = aeb.alloc_stats()
+        aeb.aeb_reduce(O, N, aeb.hist_spec(), S)
+        st = aeb.stats_from_buffer(S)
+        out[name] = {"ms": ms, "rollouts_per_s": N / (ms / 1e3), "p_contact": st.n_contact / st.n,
+                     "steps_per_rollout": st.steps / N}
+    del P, O
+    return {"samples": N, "ttc_thr_s": 2.0,
+            "readings": {"sigma_m": 1.0, "drop": 0.2, "latency_s": 0.05}, **out,
+            "precision": "fp32-compensated"}
+
+
 def config(args, world):
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         "10 s horizon, lead at d0, per-axle caps, immediate trigger",
@@ -467,7 +500,7 @@ def main():
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
-    batched = sweep = dts = moving = None
+    batched = sweep = dts = moving = percep = None
     if not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
@@ -476,6 +509,8 @@ def main():
         dts = dt_study(aeb, torch)
         torch.cuda.empty_cache()
         moving = moving_lead_run(aeb, torch)
+        torch.cuda.empty_cache()
+        percep = perception_run(aeb, torch)
 
     if rank != 0:
         if dist:
@@ -518,6 +553,7 @@ def main():
         "ttc_sweep": sweep,
         "dt_study": dts,
         "moving_lead": moving,
+        "perception": percep,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
         "steps_per_rollout": steps_per_launch / N,

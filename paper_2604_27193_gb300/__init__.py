@@ -25,7 +25,7 @@ OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
 OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
               "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
               "n_onset": np.int32}
-ABI_VERSION = 2  # AEB_ABI_VERSION of include/aeb.h
+ABI_VERSION = 3  # AEB_ABI_VERSION of include/aeb.h
 NBINS = 4096
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)
@@ -47,7 +47,8 @@ class Model(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "g", "rho", "area", "h_cg", "wheelbase", "beta", "phi_f", "a_cmd", "dt", "t_max",
         "ttc_thr")] + [(n, C.c_int32) for n in ("cap_mode", "trigger", "lead", "reserved")] + [
-        (n, C.c_double) for n in ("lead_v0", "lead_decel")]
+        (n, C.c_double) for n in ("lead_v0", "lead_decel", "perc_sigma", "perc_drop",
+                                  "perc_latency")] + [("perc_seed", C.c_uint64)]
 
 
 class Dist(C.Structure):

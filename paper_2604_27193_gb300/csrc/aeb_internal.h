@@ -18,6 +18,11 @@ struct ModelDev {
     // moving lead: initial speed, deceleration, stop time v/b (inf if b = 0),
     // stop position (v t_s) / 2 (the same binary64 expressions as the oracle)
     double lead_v0, lead_decel, lead_ts, lead_xs;
+    // per-step perception of the TTC trigger: noise scale, dropout
+    // probability, latency in steps, stream key; perc = any of them set
+    double perc_sigma, perc_drop;
+    uint64_t perc_seed;
+    int32_t perc_lat, perc;
     int32_t n_max, cap_mode, trigger, lead;
     int32_t lead_moving;  // lead && lead_v0 > 0
 };

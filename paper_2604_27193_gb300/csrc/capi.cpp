@@ -53,7 +53,8 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
     if (!m) return fail(AEB_EINVAL, "model is NULL");
     const double v[] = {m->g, m->rho, m->area, m->h_cg, m->wheelbase, m->beta,
                         m->phi_f, m->a_cmd, m->dt, m->t_max, m->ttc_thr,
-                        m->lead_v0, m->lead_decel};
+                        m->lead_v0, m->lead_decel, m->perc_sigma, m->perc_drop,
+                        m->perc_latency};
     for (double x : v)
         if (!std::isfinite(x)) return fail(AEB_EINVAL, "model constant is not finite");
     if (!(m->dt > 0.0)) return fail(AEB_EINVAL, "model.dt must be > 0");
@@ -67,6 +68,10 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
     if (m->reserved != 0) return fail(AEB_EINVAL, "model.reserved must be 0");
     if (m->lead_v0 < 0.0 || m->lead_decel < 0.0)
         return fail(AEB_EINVAL, "model.lead_v0 and model.lead_decel must be >= 0");
+    if (m->perc_sigma < 0.0 || m->perc_latency < 0.0 || m->perc_drop < 0.0 || m->perc_drop > 1.0)
+        return fail(AEB_EINVAL, "model.perc_sigma, perc_latency >= 0 and perc_drop in [0, 1]");
+    const int64_t perc_lat = steps_to_reach_host(m->perc_latency, m->dt);
+    if (perc_lat > 1000000000) return fail(AEB_EINVAL, "model.perc_latency / model.dt too large");
     const int64_t n_max = steps_to_reach_host(m->t_max, m->dt);
     if (n_max > 2147483646) return fail(AEB_EINVAL, "model.t_max / model.dt exceeds 2^31 - 2 steps");
     out->g = m->g;
@@ -90,6 +95,11 @@ aeb_status check_model(const aeb_model *m, ModelDev *out)
                                          : std::numeric_limits<double>::infinity();
     out->lead_xs = 0.5 * (m->lead_v0 * out->lead_ts);
     out->lead_moving = (m->lead == 1 && m->lead_v0 > 0.0) ? 1 : 0;
+    out->perc_sigma = m->perc_sigma;
+    out->perc_drop = m->perc_drop;
+    out->perc_seed = m->perc_seed;
+    out->perc = (m->perc_sigma > 0.0 || m->perc_drop > 0.0 || m->perc_latency > 0.0) ? 1 : 0;
+    out->perc_lat = out->perc ? (int32_t)perc_lat : 0;
     return AEB_OK;
 }
 

@@ -104,6 +104,29 @@ struct WarpQueue {
     }
 };
 
+// Philox-4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011): the block of counter
+// c under key (k0, k1), in place.  Used for the per-step perception readings
+// of the TTC trigger, counter (parameter row, step, 0, 0), key (seed,
+// kPercKey1).
+constexpr uint64_t kPercKey1 = 0x5045524345505431ull;  // "PERCEPT1"
+__device__ __forceinline__ void philox_block(uint64_t c[4], uint64_t k0, uint64_t k1)
+{
+    constexpr uint64_t kM0 = 0xD2E7470EE14C6C93ull, kM1 = 0xCA5A826395121157ull;
+    constexpr uint64_t kW0 = 0x9E3779B97F4A7C15ull, kW1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t h0 = __umul64hi(kM0, c[0]), l0 = kM0 * c[0];
+        const uint64_t h1 = __umul64hi(kM1, c[2]), l1 = kM1 * c[2];
+        const uint64_t n0 = h1 ^ c[1] ^ k0, n2 = h0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = l1;
+        c[2] = n2;
+        c[3] = l0;
+        k0 += kW0;
+        k1 += kW1;
+    }
+}
+
 // A sample is invalid if any field is not finite, mass <= 0, or tau, mu, C_d
 // or the delay is negative.
 __device__ __forceinline__ bool sample_valid(const double f[AEB_NFIELDS])

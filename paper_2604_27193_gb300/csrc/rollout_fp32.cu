@@ -96,6 +96,11 @@ struct ModelF32 {
     // moving lead: step, initial speed, deceleration, half of it, stop time,
     // stop position (binary32 copies of the model's values)
     float dt, lv0, lb, lhb, lts, lxs;
+    // per-step perception of the TTC trigger (see the model): noise scale,
+    // dropout probability, latency in steps, stream key, any of them set
+    float psig, pdrop;
+    uint64_t pseed;
+    int plat, perc;
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -524,9 +529,25 @@ struct Lane32 {
         // falls by its speed
         if (LEAD == kLeadMoving)
             m = m + fmaf(thr_h, lead_speed(F, n, cf(L_S)), lead_gap(F, n, cf(L_SIGMA)));
-        if (m <= 0.0f) {
+        // per-step perception: the reading of step n + L (its noise, in the
+        // margin's units; no test if it is missing); uniforms from the top 24
+        // bits of the Philox words
+        bool reading = true;
+        float pn = 0.0f;
+        if (F.perc) {
+            uint64_t c[4] = {pidx(), (uint64_t)((long long)n + F.plat), 0, 0};
+            philox_block(c, F.pseed, kPercKey1);
+            const float s24 = 5.9604644775390625e-8f;  // 2^-24
+            const float u1 = (float)(uint32_t)(c[0] >> 40) * s24;
+            const float u2 = (float)(uint32_t)(c[1] >> 40) * s24;
+            const float u3 = (float)(uint32_t)(c[2] >> 40) * s24;
+            const float u4 = (float)(uint32_t)(c[3] >> 40) * s24;
+            reading = !(u4 < F.pdrop);
+            pn = cf(L_SIGMA) * (F.psig * (2.0f * (((u1 + u2) + u3) - 1.5f)));
+        }
+        if (reading && m + pn <= 0.0f) {
             trig = true;
-            const long long nb = (long long)n + ci(L_NDELAY);
+            const long long nb = ((long long)n + F.plat) + ci(L_NDELAY);
             const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
             set_ci(L_NB, n_b);
             ev = (n_b < n_last) ? n_b : n_last;
@@ -537,7 +558,11 @@ struct Lane32 {
         // (a braking lead's speed term falls by thr' s dt b_L per step more;
         // its travel only widens the gap)
         const float d = fmaf(6.0f, W, thr_h * sdt * (acc + F.lb)) * 1.001f;
-        const float r = __fdividef(m, d) * 0.999f;
+        // a reading's noise is at most 3 perc_sigma: only a margin beyond that
+        // rules a trigger out whatever the readings of the skipped steps
+        const float mw = F.perc ? fmaf(-3.0f * F.psig, cf(L_SIGMA), m) : m;
+        const float r = __fdividef(mw, d) * 0.999f;
+        if (!(r > 0.0f)) return 1;
         return r >= (float)(AEB_FP32_WINDOW - 1) ? AEB_FP32_WINDOW : 1 + (int)r;
     }
 
@@ -882,6 +907,11 @@ ModelF32 to_f32(const ModelDev &m)
     f.lhb = (float)(0.5 * m.lead_decel);
     f.lts = (float)m.lead_ts;
     f.lxs = (float)m.lead_xs;
+    f.psig = (float)m.perc_sigma;
+    f.pdrop = (float)m.perc_drop;
+    f.pseed = m.perc_seed;
+    f.plat = m.perc_lat;
+    f.perc = m.perc;
     return f;
 }
 

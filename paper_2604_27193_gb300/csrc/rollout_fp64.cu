@@ -53,6 +53,7 @@ struct Lane64 {
     double d0, gs, noise, k, it, thr;
     double mg, f0, f1, r0, r1, cap;
     double pa, pb, dlo, dhi;      // current line pa + pb D (piece 1, 2) and its interval
+    uint64_t row;                 // parameter row (counter of the perception readings)
     int32_t n, n_b, n_delay;
     int piece;                    // 0: D, 1, 2: an axle line, 3: the constant cap; -1: none
     bool trig, lagged, ordered;
@@ -146,6 +147,7 @@ struct Lane64 {
             store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
             return true;
         }
+        row = pi;
         d0 = f[kD0];
         gs = f[kGs];
         noise = f[kNoise];
@@ -202,9 +204,19 @@ struct Lane64 {
                 gap_meas = (d0 - x) + noise;
                 closing = v;
             }
-            if (gap_meas <= thr * closing) {
+            bool reading = true;
+            if (M.perc) {  // the reading of step n + L describes step n
+                uint64_t c[4] = {row, (uint64_t)((long long)n + M.perc_lat), 0, 0};
+                philox_block(c, M.perc_seed, kPercKey1);
+                const double s53 = 1.0 / 9007199254740992.0;  // 2^-53
+                const double u1 = (double)(c[0] >> 11) * s53, u2 = (double)(c[1] >> 11) * s53;
+                const double u3 = (double)(c[2] >> 11) * s53, u4 = (double)(c[3] >> 11) * s53;
+                if (u4 < M.perc_drop) reading = false;
+                else gap_meas = gap_meas + M.perc_sigma * (2.0 * (((u1 + u2) + u3) - 1.5));
+            }
+            if (reading && gap_meas <= thr * closing) {
                 trig = true;
-                long long nb = (long long)n + n_delay;
+                long long nb = ((long long)n + M.perc_lat) + n_delay;
                 n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
             }
         }
