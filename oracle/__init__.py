@@ -101,6 +101,9 @@ def lib():
             L.om_steps_to_reach.restype = C.c_int64
             L.om_perception.argtypes = [P(_Model), C.c_uint64, C.c_int64, P(C.c_double)]
             L.om_perception.restype = C.c_int
+            L.om_sample_is.argtypes = [P(_Model), P(_Scenario), P(_Scenario), C.c_uint64,
+                                       C.c_uint64, P(P(C.c_double)), P(C.c_double)]
+            L.om_sample_is.restype = C.c_int
             _lib = L
     return _lib
 
@@ -157,6 +160,30 @@ def sample(model, scenario, first: int, n: int) -> dict:
     m, s = _model(model), _scenario(scenario)
     lib().om_sample(C.byref(m), C.byref(s), first, n, arr)
     return out
+
+
+def sample_is(model, nominal, proposal, first: int, n: int):
+    """Parameter sets drawn from ``proposal`` (as ``sample`` draws them) and
+    their likelihood ratios p(xi) / q(xi) to ``nominal``: (columns, weights)."""
+    out = {f: np.empty(n, dtype=np.float64) for f in FIELDS}
+    w = np.empty(n, dtype=np.float64)
+    arr = (C.POINTER(C.c_double) * 10)(*[_dptr(out[f]) for f in FIELDS])
+    m, sp, sq = _model(model), _scenario(nominal), _scenario(proposal)
+    if lib().om_sample_is(C.byref(m), C.byref(sp), C.byref(sq), first, n, arr, _dptr(w)) != 0:
+        raise ValueError("proposal incompatible with the nominal scenario")
+    return out, w
+
+
+def is_estimate(weights, event):
+    """Importance-sampling estimate of P(event) under the nominal scenario, its
+    standard error and the 95 % normal interval (plain definitions, fsum)."""
+    import math
+    n = len(weights)
+    y = np.where(event, weights, 0.0)
+    p = math.fsum(y) / n
+    var = (math.fsum(y * y) - n * p * p) / (n - 1)
+    se = math.sqrt(max(var, 0.0) / n)
+    return p, se, (p - 1.959963984540054 * se, p + 1.959963984540054 * se)
 
 
 # --------------------------------------------------------------------------

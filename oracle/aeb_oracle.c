@@ -37,6 +37,9 @@
  *   om_perception      pinned: numpy's Philox-4x64-10 per reading, the exact
  *                      Irwin-Hall CDF, dropout frequency; the trigger step of
  *                      coasting cars against a brute-force search, latency shift.
+ *   om_sample_is       pinned: draws equal om_sample's from the proposal; weights
+ *                      against scipy densities and tail masses; unbiasedness;
+ *                      a rare event with an exact probability.
  *   om_axle_cap        pinned: brute-force fixed-point iteration of the per-axle
  *                      force balance.
  *   om_reduce          pinned: numpy / math.fsum brute force over the outputs.
@@ -183,6 +186,97 @@ int om_sample(const om_model *m, const om_scenario *sc, uint64_t first, uint64_t
             q[qa] = draw(&sc->dist[qa], w[0], w[1]);
             if (qb < S_COUNT) q[qb] = draw(&sc->dist[qb], w[2], w[3]);
         }
+        cols[F_V0][j] = q[S_V0];
+        cols[F_D0][j] = q[S_D0];
+        cols[F_MU][j] = q[S_MU];
+        cols[F_GS][j] = m->g * sin(q[S_GRADE]);
+        cols[F_GC][j] = m->g * cos(q[S_GRADE]);
+        cols[F_MASS][j] = q[S_MASS];
+        cols[F_CD][j] = q[S_CD];
+        cols[F_TAU][j] = q[S_TAU];
+        cols[F_TDELAY][j] = q[S_TDELAY];
+        cols[F_NOISE][j] = q[S_NOISE];
+    }
+    return 0;
+}
+
+/*
+ * Importance sampling (extension; Sec. VIII names rare-event estimation of
+ * low collision probabilities as future work).  Parameter sets are drawn from
+ * a proposal scenario q exactly as om_sample draws them, and each carries the
+ * likelihood ratio w = p(xi) / q(xi) to the nominal scenario p, the product
+ * over the nine quantities of one quantity's ratio for its clamped value x:
+ *   constant: 1 (p and q must agree);
+ *   an atom at a clamp bound (the bound holds probability mass under q):
+ *     P_p(X <= lo) / P_q(X <= lo), or the upper tails at hi;
+ *   otherwise the density ratio: uniform 1[a_p <= x < b_p] (b_q - a_q)/(b_p - a_p),
+ *     normal (s_q / s_p) exp(z_q^2 / 2 - z_p^2 / 2), z = (x - mean) / sd.
+ * p and q must have the same kind and clamp bounds per quantity, and a
+ * uniform q must cover p's interval (else om_sample_is returns -1).  Then
+ * E_q[w f(xi)] = E_p[f(xi)] for any outcome f.
+ */
+static double cdf_dist(const om_dist *d, double x) /* P(unclamped draw <= x) */
+{
+    if (d->kind == OM_DIST_UNIFORM) {
+        double u = (x - d->p0) / (d->p1 - d->p0);
+        return u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+    }
+    return 0.5 * erfc(-((x - d->p0) / d->p1) / sqrt(2.0));
+}
+
+static double sf_dist(const om_dist *d, double x) /* P(unclamped draw > x) */
+{
+    if (d->kind == OM_DIST_UNIFORM) return 1.0 - cdf_dist(d, x);
+    return 0.5 * erfc(((x - d->p0) / d->p1) / sqrt(2.0));
+}
+
+static double quantity_ratio(const om_dist *p, const om_dist *q, double x)
+{
+    if (q->kind == OM_DIST_CONST) return 1.0;
+    if (x <= q->lo) {
+        double mq = cdf_dist(q, q->lo);
+        if (mq > 0.0) return cdf_dist(p, p->lo) / mq;
+    }
+    if (x >= q->hi) {
+        double mq = sf_dist(q, q->hi);
+        if (mq > 0.0) return sf_dist(p, p->hi) / mq;
+    }
+    if (q->kind == OM_DIST_UNIFORM) {
+        if (!(x >= p->p0 && x < p->p1)) return 0.0;
+        return (q->p1 - q->p0) / (p->p1 - p->p0);
+    }
+    double zp = (x - p->p0) / p->p1, zq = (x - q->p0) / q->p1;
+    return (q->p1 / p->p1) * exp(0.5 * (zq * zq) - 0.5 * (zp * zp));
+}
+
+static int is_compatible(const om_dist *p, const om_dist *q)
+{
+    if (p->kind != q->kind || p->lo != q->lo || p->hi != q->hi) return 0;
+    if (q->kind == OM_DIST_CONST) return p->p0 == q->p0;
+    if (q->kind == OM_DIST_UNIFORM) return q->p0 <= p->p0 && p->p1 <= q->p1 && p->p1 > p->p0;
+    return p->p1 > 0.0 && q->p1 > 0.0;
+}
+
+int om_sample_is(const om_model *m, const om_scenario *nominal, const om_scenario *proposal,
+                 uint64_t first, uint64_t n, double *const cols[OM_NFIELDS], double *weights)
+{
+    for (int k = 0; k < S_COUNT; ++k)
+        if (!is_compatible(&nominal->dist[k], &proposal->dist[k])) return -1;
+    const uint64_t key[2] = { proposal->seed, proposal->scenario_id };
+    for (uint64_t j = 0; j < n; ++j) {
+        uint64_t i = first + j;
+        double q[S_COUNT + 1];
+        for (int b = 0; b < 5; ++b) {
+            uint64_t ctr[4] = { i, (uint64_t)b, 0, 0 }, w[4];
+            om_philox4x64_10(ctr, key, w);
+            int qa = 2 * b, qb = 2 * b + 1;
+            q[qa] = draw(&proposal->dist[qa], w[0], w[1]);
+            if (qb < S_COUNT) q[qb] = draw(&proposal->dist[qb], w[2], w[3]);
+        }
+        double wt = 1.0;
+        for (int k = 0; k < S_COUNT; ++k)
+            wt *= quantity_ratio(&nominal->dist[k], &proposal->dist[k], q[k]);
+        weights[j] = wt;
         cols[F_V0][j] = q[S_V0];
         cols[F_D0][j] = q[S_D0];
         cols[F_MU][j] = q[S_MU];

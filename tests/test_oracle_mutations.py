@@ -45,6 +45,11 @@ MUTATIONS = [
     ("latency onset", "n_b = (n + lat) + c->n_delay;", "n_b = n + c->n_delay;"),
     ("reading index", "reading = perception(m, row, n + lat, &pn);",
      "reading = perception(m, row, n, &pn);"),
+    ("IS normal ratio sign", "exp(0.5 * (zq * zq) - 0.5 * (zp * zp))",
+     "exp(0.5 * (zp * zp) - 0.5 * (zq * zq))"),
+    ("IS uniform ratio inverted", "return (q->p1 - q->p0) / (p->p1 - p->p0);",
+     "return (p->p1 - p->p0) / (q->p1 - q->p0);"),
+    ("IS atom ignored", "if (mq > 0.0) return cdf_dist(p, p->lo) / mq;", "if (mq < 0.0) return 1.0;"),
 ]
 
 
@@ -60,7 +65,7 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
     env = dict(os.environ, AEB_ORACLE_SO=str(so))
     tests = [os.path.join(ROOT, "tests", f) for f in
              ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py",
-              "test_oracle_perception.py")]
+              "test_oracle_perception.py", "test_oracle_is.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         *tests], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, f"mutation '{name}' survived:\n{r.stdout[-2000:]}"
