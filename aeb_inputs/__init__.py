@@ -209,6 +209,13 @@ def lead_braking_scenario(seed: int = 0, scenario_id: int = 0) -> Scenario:
     return Scenario(d0=uniform(12.0, 40.0), seed=seed, scenario_id=scenario_id)
 
 
+def rare_event_proposal(nominal: Scenario, scenario_id: int = 7) -> Scenario:
+    """Importance-sampling proposal for long stops of the paper preset (Eq. 11-15):
+    faster cars, lower friction, downhill, same kinds and clamp bounds."""
+    return replace(nominal, v0=normal(34.0, 2.5), mu=normal(0.62, 0.11),
+                   grade=normal(-0.02, 0.05), scenario_id=scenario_id)
+
+
 def ttc_model(thr: float = 2.0, dt: float = 1e-3) -> Model:
     return Model(dt=dt, trigger=TRIGGER_TTC, ttc_thr=thr)
 

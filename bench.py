@@ -18,8 +18,9 @@ so no flush is needed between steps.
 Beside the headline the line carries the serving run (Poisson requests,
 latency percentiles), the scenario-grid batched run, the TTC-threshold sweep and
 a coarse-step study (the same samples at dt = 0.1 .. 20 ms: speed and the error
-against the 0.1 ms rollouts), a moving-lead run (a lead braking ahead) and a
-TTC run with noisy, late and missing readings; `--no-extras` skips the last five.
+against the 0.1 ms rollouts), a moving-lead run (a lead braking ahead), a TTC
+run with noisy, late and missing readings and a rare-event estimate (plain Monte
+Carlo against importance sampling); `--no-extras` skips the last six.
 
 `--impl reference` times the plain CPU oracle on a bounded sample of the same
 workload on the host cores (the CPU baseline), with the same metric.
@@ -355,6 +356,51 @@ def perception_run(aeb, torch):
             "precision": "fp32-compensated"}
 
 
+def rare_event_run(aeb, torch):
+    """Rare-event estimation for the paper preset (Eq. 11-15): P(D_stop > 135 m)
+    by plain Monte Carlo on 1e7 nominal samples and by importance sampling on
+    1e6 samples of a proposal (faster cars, lower friction, downhill) with
+    likelihood-ratio weights (FP32-compensated rollouts, device-resident inputs;
+    the time is the rollout plus the reduction).  The variance reduction is
+    p (1 - p) over the weighted estimator's variance per sample."""
+    import math
+    m = ai.paper_model()
+    nominal = ai.paper_scenario(seed=11)
+    h0 = 135.0
+    res = {}
+    for name, n in (("plain", 10_000_000), ("importance", 1_000_000)):
+        if name == "plain":
+            cols = aeb.aeb_sample_params(m, nominal, 0, n)
+            w = np.ones(n)
+        else:
+            cols, w = aeb.aeb_sample_params_is(m, nominal, ai.rare_event_proposal(nominal), 0, n)
+        P = {f: torch.from_numpy(cols[f]).cuda() for f in ai.FIELDS}
+        W = torch.from_numpy(w).cuda()
+        O = aeb.alloc_outputs(n, which=("status", "x_ref"))
+        S = torch.zeros(aeb.WSTATS_BYTES, dtype=torch.uint8, device="cuda")
+        aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+        aeb.aeb_reduce_weighted(O, W, n, h0, S)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        est, se, ci = aeb.is_estimate(aeb.wstats_from_buffer(S))
+        res[name] = {"samples": n, "ms": ms, "p": est, "se": se, "ci95": list(ci)}
+        del P, W, O
+    pl, im = res["plain"], res["importance"]
+    p_ref = pl["p"]
+    vr = p_ref * (1 - p_ref) / (im["se"] ** 2 * im["samples"]) if im["se"] > 0 else None
+    # time to reach the same standard error: t * se^2 scales as 1 / samples
+    speedup = (pl["ms"] * pl["se"] ** 2) / (im["ms"] * im["se"] ** 2) if im["se"] > 0 else None
+    return {"event": "D_stop > 135 m (paper preset, no lead)", **res,
+            "variance_reduction_per_sample": vr, "time_to_equal_se_speedup": speedup,
+            "z_between_estimates": (im["p"] - pl["p"]) / math.hypot(im["se"], pl["se"]),
+            "precision": "fp32-compensated"}
+
+
 def config(args, world):
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         "10 s horizon, lead at d0, per-axle caps, immediate trigger",
@@ -500,7 +546,7 @@ def main():
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
-    batched = sweep = dts = moving = percep = None
+    batched = sweep = dts = moving = percep = rare = None
     if not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
@@ -511,6 +557,8 @@ def main():
         moving = moving_lead_run(aeb, torch)
         torch.cuda.empty_cache()
         percep = perception_run(aeb, torch)
+        torch.cuda.empty_cache()
+        rare = rare_event_run(aeb, torch)
 
     if rank != 0:
         if dist:
@@ -554,6 +602,7 @@ def main():
         "dt_study": dts,
         "moving_lead": moving,
         "perception": percep,
+        "rare_event": rare,
         "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
         "rk4_steps_per_s": world * steps_per_launch * args.steps / (ms_total / 1e3),
         "steps_per_rollout": steps_per_launch / N,

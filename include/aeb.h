@@ -235,6 +235,13 @@ typedef struct aeb_serve_counters {
 /* Opaque serving engine. */
 typedef struct aeb_server aeb_server;
 
+/* Weighted event sums of an importance-sampled set (aeb_reduce_weighted). */
+typedef struct aeb_wstats {
+    uint64_t n, n_valid, n_event;  /* samples, valid samples, valid samples in E   */
+    double sum_w, sumsq_w;         /* sum of w and of w^2 over valid samples       */
+    double sum_we, sumsq_we;       /* sum of w 1[E] and of (w 1[E])^2              */
+} aeb_wstats;
+
 /* Collision probability at one TTC threshold, pooled over the scenarios
  * (Sec. VI-C, Eq. 19 with the TTC = H0 / v criterion). */
 typedef struct aeb_sweep_result {
@@ -269,6 +276,43 @@ const char *aeb_last_error(void);
 aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenario *scenario,
                              uint64_t first, uint64_t n, const aeb_params *out,
                              int32_t n_threads);
+
+/*
+ * aeb_sample_params_is -- importance sampling (extension: rare-event
+ * estimation of low collision probabilities), first half: draw parameter sets
+ * from `proposal` exactly as aeb_sample_params does and write each set's
+ * likelihood ratio w = p(xi) / q(xi) to `nominal`: the product over the
+ * quantities of, for the clamped value x, 1 for a constant, the ratio of the
+ * probability masses the two laws put at a clamp bound if x sits on one that
+ * holds mass under q, else the ratio of the densities (uniform:
+ * 1[a_p <= x < b_p] (b_q - a_q) / (b_p - a_p); normal: (s_q / s_p)
+ * exp((z_q^2 - z_p^2) / 2)).  Then E_q[w f] = E_p[f] for any outcome f.
+ *   weights  host array of n doubles (caller-owned)
+ * Synchronous, host only; independent of n_threads.  AEB_EINVAL: NULL pointer,
+ * invalid distribution, or a proposal incompatible with `nominal` (per
+ * quantity: same kind and clamp bounds, equal constants, a uniform proposal
+ * covering the nominal interval, positive normal sds).
+ */
+aeb_status aeb_sample_params_is(const aeb_model *model, const aeb_scenario *nominal,
+                                const aeb_scenario *proposal, uint64_t first, uint64_t n,
+                                const aeb_params *out, double *weights, int32_t n_threads);
+
+/*
+ * aeb_reduce_weighted -- importance sampling, second half: over valid samples,
+ * the sums of w, w^2, w 1[E] and (w 1[E])^2 for the event E = contact, or
+ * x_ref > x_thr (P(D_stop > H0), Sec. VI-C; x_thr = +inf: contact only).
+ * Then sum_we / n estimates the nominal probability of E without bias, with
+ * standard error sqrt((sumsq_we / n - p^2) / (n - 1)).
+ *   out      DEVICE outputs; status and x_ref required
+ *   weights  DEVICE array of n likelihood ratios (aeb_sample_params_is)
+ *   stats    DEVICE aeb_wstats written (fixed summation order: the same bits
+ *            for the same inputs)
+ * Asynchronous on `stream`.  AEB_EINVAL: NULL pointers, misaligned stats, NaN
+ * x_thr.
+ */
+aeb_status aeb_reduce_weighted(const aeb_outputs *out, const double *weights, uint64_t n,
+                               double x_thr, aeb_wstats *stats, void *stream);
+
 
 /*
  * aeb_rollout -- integrate every sample until contact, stop or horizon

@@ -119,7 +119,13 @@ class SweepResult(C.Structure):
         [(n, C.c_double) for n in ("p_contact", "ci_lo", "ci_hi")]
 
 
+class WStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n", "n_valid", "n_event")] + [
+        (n, C.c_double) for n in ("sum_w", "sumsq_w", "sum_we", "sumsq_we")]
+
+
 STATS_BYTES = C.sizeof(Stats)
+WSTATS_BYTES = C.sizeof(WStats)
 JOB_STATS_BYTES = C.sizeof(JobStats)
 
 _lib = None
@@ -144,6 +150,10 @@ def lib():
             L.aeb_last_error.restype = C.c_char_p
             L.aeb_sample_params.argtypes = [P(Model), P(Scenario), C.c_uint64, C.c_uint64,
                                             P(Params), C.c_int32]
+            L.aeb_sample_params_is.argtypes = [P(Model), P(Scenario), P(Scenario), C.c_uint64,
+                                               C.c_uint64, P(Params), C.c_void_p, C.c_int32]
+            L.aeb_reduce_weighted.argtypes = [P(Outputs), C.c_void_p, C.c_uint64, C.c_double,
+                                              C.c_void_p, C.c_void_p]
             L.aeb_rollout.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32, P(Outputs),
                                       C.c_void_p]
             L.aeb_reduce.argtypes = [P(Outputs), C.c_uint64, P(HistSpec), C.c_void_p,
@@ -173,7 +183,8 @@ def lib():
                        "aeb_batch_create", "aeb_batch_run", "aeb_rollout_batched",
                        "aeb_get_launch_config", "aeb_set_launch_config", "aeb_autotune",
                        "aeb_serve_create", "aeb_serve_submit", "aeb_serve_poll",
-                       "aeb_serve_cancel", "aeb_serve_counters_get"):
+                       "aeb_serve_cancel", "aeb_serve_counters_get", "aeb_sample_params_is",
+                       "aeb_reduce_weighted"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != ABI_VERSION:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -261,6 +272,45 @@ def aeb_sample_params(m, sc, first: int, n: int, out: dict | None = None,
     ms, ss, ps = model(m), scenario(sc), params_struct(out)
     _check(lib().aeb_sample_params(C.byref(ms), C.byref(ss), first, n, C.byref(ps), n_threads))
     return out
+
+
+def aeb_sample_params_is(m, nominal, proposal, first: int, n: int, out: dict | None = None,
+                         weights=None, n_threads: int = 0):
+    """Importance sampling: host draws from ``proposal`` and their likelihood
+    ratios to ``nominal``; returns (columns, weights)."""
+    if out is None:
+        out = {f: np.empty(n, dtype=np.float64) for f in FIELDS}
+    if weights is None:
+        weights = np.empty(n, dtype=np.float64)
+    ms, ps = model(m), params_struct(out)
+    sn, sq = scenario(nominal), scenario(proposal)
+    _check(lib().aeb_sample_params_is(C.byref(ms), C.byref(sn), C.byref(sq), first, n,
+                                      C.byref(ps), C.c_void_p(_ptr(weights)), n_threads))
+    return out, weights
+
+
+def aeb_reduce_weighted(out: dict, weights, n: int, x_thr: float, wstats_dev, stream=None):
+    """Asynchronous weighted event sums into ``wstats_dev`` (``WSTATS_BYTES``
+    bytes of device memory); event = contact or x_ref > x_thr."""
+    os_ = outputs_struct(out)
+    _check(lib().aeb_reduce_weighted(C.byref(os_), C.c_void_p(_ptr(weights)), n,
+                                     C.c_double(x_thr), C.c_void_p(_ptr(wstats_dev)),
+                                     _stream(stream)))
+
+
+def wstats_from_buffer(buf) -> WStats:
+    raw = buf.cpu().numpy().tobytes() if hasattr(buf, "cpu") else bytes(buf)
+    return WStats.from_buffer_copy(raw)
+
+
+def is_estimate(ws: WStats):
+    """Unbiased importance-sampling estimate of the event probability under the
+    nominal law, its standard error and the 95 % normal interval."""
+    n = ws.n
+    p = ws.sum_we / n
+    var = (ws.sumsq_we - n * p * p) / (n - 1) if n > 1 else float("nan")
+    se = float(np.sqrt(max(var, 0.0) / n))
+    return p, se, (p - 1.959963984540054 * se, p + 1.959963984540054 * se)
 
 
 def aeb_rollout(m, params: dict, n: int, precision: int, out: dict, stream=None):

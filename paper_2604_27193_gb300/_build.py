@@ -28,6 +28,7 @@ CU_SOURCES = {
     "rollout_fp32.cu": ["-fmad=false"],
     "reduce.cu": [],
     "reduce_noalloc.cu": [],
+    "reduce_weighted.cu": [],
     "peaks.cu": ["-fmad=true"],
 }
 CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp", "sweep.cpp"]

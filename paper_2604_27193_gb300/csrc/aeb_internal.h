@@ -105,4 +105,12 @@ aeb_status check_params(const aeb_params *p, ParamsDev *out);
 OutDev out_dev(const aeb_outputs *o);
 aeb_status cuda_fail(cudaError_t e, const char *what);
 
+// Weighted event sums for importance sampling (reduce_weighted.cu): at most
+// kWMaxBlocks partials in `partials` (weighted_partial_bytes() bytes).
+constexpr int kWMaxBlocks = 1024;
+size_t weighted_partial_bytes();
+cudaError_t launch_reduce_weighted(const uint8_t *status, const double *x_ref, const double *w,
+                                   uint64_t n, double x_thr, void *partials, aeb_wstats *stats,
+                                   cudaStream_t s);
+
 }  // namespace aeb

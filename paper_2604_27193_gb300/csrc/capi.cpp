@@ -327,6 +327,29 @@ extern "C" aeb_status aeb_reduce(const aeb_outputs *out, uint64_t n, const aeb_h
     return reduce_impl(out, n, *hist, stats, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" aeb_status aeb_reduce_weighted(const aeb_outputs *out, const double *weights,
+                                          uint64_t n, double x_thr, aeb_wstats *stats,
+                                          void *stream)
+{
+    clear_error();
+    if (!out || !stats || (n > 0 && (!weights || !out->status || !out->x_ref)))
+        return fail(AEB_EINVAL, "aeb_reduce_weighted: NULL argument (status, x_ref, weights "
+                                "and stats are required)");
+    if (reinterpret_cast<uintptr_t>(stats) % 8 != 0 ||
+        reinterpret_cast<uintptr_t>(weights) % 8 != 0)
+        return fail(AEB_EINVAL, "aeb_reduce_weighted: stats or weights not 8-byte aligned");
+    if (std::isnan(x_thr)) return fail(AEB_EINVAL, "aeb_reduce_weighted: x_thr is NaN");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    aeb_status st = scratch_for(s, kCounterBytes + partial_bytes(), &scratch);
+    if (st != AEB_OK) return st;
+    static_assert(sizeof(RedPartial) * 1024 >= 48 * 1024, "scratch too small for weighted partials");
+    cudaError_t e = launch_reduce_weighted(out->status, out->x_ref, weights, n, x_thr,
+                                           static_cast<char *>(scratch) + kCounterBytes, stats, s);
+    if (e != cudaSuccess) return cuda_fail(e, "aeb_reduce_weighted launch");
+    return AEB_OK;
+}
+
 extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64_t n,
                                    aeb_precision precision, const aeb_hist_spec *hist,
                                    aeb_stats *host_stats, const aeb_outputs *host_out,

@@ -68,11 +68,66 @@ inline double transform(const aeb_dist &d, uint64_t w0, uint64_t w1)
     return x;
 }
 
+// Importance sampling: probability that an unclamped draw of d lies at or
+// below x, or above x.
+double mass_below(const aeb_dist &d, double x)
+{
+    if (d.kind == AEB_DIST_UNIFORM) {
+        const double u = (x - d.p0) / (d.p1 - d.p0);
+        return u <= 0.0 ? 0.0 : (u >= 1.0 ? 1.0 : u);
+    }
+    return 0.5 * std::erfc((d.p0 - x) / (d.p1 * std::sqrt(2.0)));
+}
+
+double mass_above(const aeb_dist &d, double x)
+{
+    if (d.kind == AEB_DIST_UNIFORM) return 1.0 - mass_below(d, x);
+    return 0.5 * std::erfc((x - d.p0) / (d.p1 * std::sqrt(2.0)));
+}
+
+// Likelihood ratio p(x) / q(x) of one quantity drawn from q with clamped
+// value x: a clamp bound holding mass under q compares the masses there,
+// elsewhere the densities compare.
+double likelihood_ratio(const aeb_dist &p, const aeb_dist &q, double x)
+{
+    if (q.kind == AEB_DIST_CONST) return 1.0;
+    if (x <= q.lo) {
+        const double mq = mass_below(q, q.lo);
+        if (mq > 0.0) return mass_below(p, p.lo) / mq;
+    }
+    if (x >= q.hi) {
+        const double mq = mass_above(q, q.hi);
+        if (mq > 0.0) return mass_above(p, p.hi) / mq;
+    }
+    if (q.kind == AEB_DIST_UNIFORM)
+        return (x >= p.p0 && x < p.p1) ? (q.p1 - q.p0) / (p.p1 - p.p0) : 0.0;
+    const double zp = (x - p.p0) / p.p1, zq = (x - q.p0) / q.p1;
+    return (q.p1 / p.p1) * std::exp(0.5 * (zq * zq - zp * zp));
+}
+
+bool is_compatible(const aeb_dist &p, const aeb_dist &q)
+{
+    if (p.kind != q.kind || p.lo != q.lo || p.hi != q.hi) return false;
+    switch (q.kind) {
+    case AEB_DIST_CONST: return p.p0 == q.p0;
+    case AEB_DIST_UNIFORM: return q.p0 <= p.p0 && p.p1 <= q.p1 && p.p1 > p.p0;
+    default: return p.p1 > 0.0 && q.p1 > 0.0;
+    }
+}
+
+// Samples [lo, hi) of the call; with `nominal`, also their likelihood ratios.
 void sample_block(double g, const aeb_scenario &sc, uint64_t first, uint64_t lo, uint64_t hi,
-                  const aeb_params &out)
+                  const aeb_params &out, const aeb_scenario *nominal, double *weights)
 {
     const aeb_dist *dist[9] = {&sc.v0, &sc.d0, &sc.mu, &sc.grade, &sc.mass,
                                &sc.cd, &sc.tau, &sc.t_delay, &sc.noise};
+    const aeb_dist *ndist[9] = {};
+    if (nominal) {
+        const aeb_dist *nd[9] = {&nominal->v0, &nominal->d0, &nominal->mu, &nominal->grade,
+                                 &nominal->mass, &nominal->cd, &nominal->tau,
+                                 &nominal->t_delay, &nominal->noise};
+        for (int q = 0; q < 9; ++q) ndist[q] = nd[q];
+    }
     for (uint64_t j = lo; j < hi; ++j) {
         double q[10];
         for (uint64_t b = 0; b < 5; ++b) {
@@ -91,6 +146,11 @@ void sample_block(double g, const aeb_scenario &sc, uint64_t first, uint64_t lo,
         out.tau[j] = q[6];
         out.t_delay[j] = q[7];
         out.noise[j] = q[8];
+        if (nominal) {
+            double w = 1.0;
+            for (int k = 0; k < 9; ++k) w *= likelihood_ratio(*ndist[k], *dist[k], q[k]);
+            weights[j] = w;
+        }
     }
 }
 
@@ -107,26 +167,37 @@ bool dist_ok(const aeb_dist &d)
 }  // namespace
 }  // namespace aeb
 
-extern "C" aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenario *scenario,
-                                        uint64_t first, uint64_t n, const aeb_params *out,
-                                        int32_t n_threads)
+namespace aeb {
+namespace {
+
+aeb_status sample_impl(const char *who, const aeb_model *model, const aeb_scenario *scenario,
+                       const aeb_scenario *nominal, uint64_t first, uint64_t n,
+                       const aeb_params *out, double *weights, int32_t n_threads)
 {
-    using namespace aeb;
-    clear_error();
-    if (!model || !scenario || !out) return fail(AEB_EINVAL, "aeb_sample_params: NULL argument");
-    if (!std::isfinite(model->g)) return fail(AEB_EINVAL, "aeb_sample_params: g is not finite");
+    const std::string w = who;
+    if (!model || !scenario || !out) return fail(AEB_EINVAL, w + ": NULL argument");
+    if (!std::isfinite(model->g)) return fail(AEB_EINVAL, w + ": g is not finite");
     const aeb_dist *dist[9] = {&scenario->v0, &scenario->d0, &scenario->mu, &scenario->grade,
                                &scenario->mass, &scenario->cd, &scenario->tau,
                                &scenario->t_delay, &scenario->noise};
     for (int q = 0; q < 9; ++q)
         if (!dist_ok(*dist[q]))
-            return fail(AEB_EINVAL, "aeb_sample_params: invalid distribution for quantity " +
-                                        std::to_string(q));
+            return fail(AEB_EINVAL, w + ": invalid distribution for quantity " + std::to_string(q));
+    if (nominal) {
+        if (!weights) return fail(AEB_EINVAL, w + ": NULL weights");
+        const aeb_dist *nd[9] = {&nominal->v0, &nominal->d0, &nominal->mu, &nominal->grade,
+                                 &nominal->mass, &nominal->cd, &nominal->tau,
+                                 &nominal->t_delay, &nominal->noise};
+        for (int q = 0; q < 9; ++q)
+            if (!dist_ok(*nd[q]) || !is_compatible(*nd[q], *dist[q]))
+                return fail(AEB_EINVAL, w + ": proposal incompatible with the nominal scenario "
+                                            "for quantity " + std::to_string(q));
+    }
     if (n == 0) return AEB_OK;
     const double *cols[AEB_NFIELDS] = {out->v0, out->d0, out->mu, out->gs, out->gc,
                                        out->mass, out->cd, out->tau, out->t_delay, out->noise};
     for (int j = 0; j < AEB_NFIELDS; ++j)
-        if (!cols[j]) return fail(AEB_EINVAL, "aeb_sample_params: NULL output column");
+        if (!cols[j]) return fail(AEB_EINVAL, w + ": NULL output column");
 
     unsigned hw = std::thread::hardware_concurrency();
     uint64_t t = n_threads > 0 ? (uint64_t)n_threads : (hw ? hw : 1);
@@ -136,7 +207,7 @@ extern "C" aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenar
     const aeb_scenario sc = *scenario;
     const aeb_params o = *out;
     if (t == 1) {
-        sample_block(model->g, sc, first, 0, n, o);
+        sample_block(model->g, sc, first, 0, n, o, nominal, weights);
         return AEB_OK;
     }
     std::vector<std::thread> pool;
@@ -144,12 +215,36 @@ extern "C" aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenar
     try {
         for (uint64_t k = 0; k < t; ++k) {
             const uint64_t lo = n * k / t, hi = n * (k + 1) / t;
-            pool.emplace_back(sample_block, model->g, std::cref(sc), first, lo, hi, std::cref(o));
+            pool.emplace_back(sample_block, model->g, std::cref(sc), first, lo, hi, std::cref(o),
+                              nominal, weights);
         }
     } catch (...) {
         for (auto &th : pool) th.join();
-        return fail(AEB_ENOMEM, "aeb_sample_params: could not start sampling threads");
+        return fail(AEB_ENOMEM, w + ": could not start sampling threads");
     }
     for (auto &th : pool) th.join();
     return AEB_OK;
+}
+
+}  // namespace
+}  // namespace aeb
+
+extern "C" aeb_status aeb_sample_params(const aeb_model *model, const aeb_scenario *scenario,
+                                        uint64_t first, uint64_t n, const aeb_params *out,
+                                        int32_t n_threads)
+{
+    aeb::clear_error();
+    return aeb::sample_impl("aeb_sample_params", model, scenario, nullptr, first, n, out,
+                            nullptr, n_threads);
+}
+
+extern "C" aeb_status aeb_sample_params_is(const aeb_model *model, const aeb_scenario *nominal,
+                                           const aeb_scenario *proposal, uint64_t first,
+                                           uint64_t n, const aeb_params *out, double *weights,
+                                           int32_t n_threads)
+{
+    aeb::clear_error();
+    if (!nominal) return aeb::fail(AEB_EINVAL, "aeb_sample_params_is: NULL nominal scenario");
+    return aeb::sample_impl("aeb_sample_params_is", model, proposal, nominal, first, n, out,
+                            weights, n_threads);
 }

@@ -187,3 +187,24 @@ def test_sampler_rejects_bad_distributions(aeb):
             aeb.aeb_sample_params(m, sc, 0, 10)
         assert e.value.code == aeb.EINVAL
     assert aeb.aeb_sample_params(m, ai.single_scenario(), 0, 0)["v0"].size == 0
+
+
+def test_importance_sampler_matches_oracle(aeb, oracle_mod):
+    """aeb_sample_params_is: the proposal draws bit for bit, the likelihood
+    ratios within 1e-12 relative of the oracle's (both via the host libm; the
+    expressions are ordered differently), independent of the thread count, and
+    incompatible proposals rejected."""
+    import numpy as np
+    m = ai.paper_model()
+    p = ai.paper_scenario(seed=5)
+    q = ai.rare_event_proposal(p)
+    cols, w = aeb.aeb_sample_params_is(m, p, q, 1000, 9_000, n_threads=3)
+    ocols, ow = oracle_mod.sample_is(m, p, q, 1000, 9_000)
+    for f in ai.FIELDS:
+        assert np.array_equal(cols[f].view(np.uint64), ocols[f].view(np.uint64)), f
+    assert np.all(np.abs(w - ow) <= 1e-12 * np.abs(ow))
+    c1, w1 = aeb.aeb_sample_params_is(m, p, q, 1000, 9_000, n_threads=1)
+    assert np.array_equal(w1.view(np.uint64), w.view(np.uint64))
+    with pytest.raises(aeb.AebError) as e:
+        aeb.aeb_sample_params_is(m, p, ai.replace(q, tau=ai.uniform(0.1, 0.2)), 0, 10)
+    assert e.value.code == aeb.EINVAL
