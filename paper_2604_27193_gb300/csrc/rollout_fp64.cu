@@ -302,8 +302,13 @@ struct Lane64 {
     }
 };
 
+#ifndef AEB_FP64_MIN_BLOCKS
+#define AEB_FP64_MIN_BLOCKS 1  // resident blocks per SM the register budget must allow
+#endif
+
 template <int CAP, bool LEAD, bool TTC>
-__global__ void __launch_bounds__(128) k_rollout_fp64(ModelDev M, ParamsDev P, OutDev O, WorkDev W)
+__global__ void __launch_bounds__(128, AEB_FP64_MIN_BLOCKS)
+k_rollout_fp64(ModelDev M, ParamsDev P, OutDev O, WorkDev W)
 {
     rollout_driver<Lane64<CAP, LEAD, TTC>>(M, NoExtra{}, P, O, W, W.tile);
 }
