@@ -178,8 +178,8 @@ typedef struct aeb_stats {
     uint64_t hist_v[AEB_NBINS];
 } aeb_stats;
 
-/* One job of a batched launch (many scenarios with uneven
- * sample counts in one persistent launch): its parameters are rows
+/* One job of a batched launch (many scenarios with uneven sample counts in
+ * one persistent launch): its parameters are rows
  * [param_offset, param_offset + n) of the device columns, its outputs rows
  * [out_offset, out_offset + n) of the output columns; ttc_thr is its own TTC
  * threshold (used when model.trigger is AEB_TRIGGER_TTC). */
@@ -206,7 +206,8 @@ typedef struct aeb_launch_config {
 /* Opaque batched-launch plan (device tables + captured CUDA graph). */
 typedef struct aeb_batch aeb_batch;
 
-/* Serving engine configuration (the 530 ms budget of Sec. VI-F). */
+/* Serving engine configuration (continuous batching of requests; the 530 ms
+ * budget of Sec. VI-F). */
 typedef struct aeb_serve_cfg {
     aeb_precision precision;      /* rollout precision of every request               */
     int32_t device;               /* CUDA device ordinal                              */
@@ -384,8 +385,8 @@ aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64
                         aeb_stats *host_stats, const aeb_outputs *host_out, void *stream);
 
 /*
- * aeb_batch_create -- plan a batched launch over n_jobs jobs (
- * the per-sample method is that of aeb_rollout, Sec. IV-D, V-A..V-D).  Builds
+ * aeb_batch_create -- plan a batched launch over n_jobs jobs (the per-sample
+ * method is that of aeb_rollout, Sec. IV-D, V-A..V-D).  Builds
  * the table of (job, tile) work items, allocates the device tables and
  * scratch (owned by the plan), and captures one CUDA graph: reset of the work
  * counter, one persistent rollout launch over all tiles, and the per-job
@@ -437,8 +438,8 @@ aeb_status aeb_autotune(const aeb_model *model, const aeb_params *params, uint64
 
 /*
  * aeb_serve_create -- start a serving engine on cfg->device for `model`
- * (continuous batching of scenario requests, latency against
- * the 530 ms Monte Carlo budget of Sec. VI-F).  A request is a scenario and a
+ * (continuous batching of scenario requests, latency against the 530 ms
+ * Monte Carlo budget of Sec. VI-F).  A request is a scenario and a
  * sample count; the engine samples it on the host (Sec. IV-C), keeps its
  * parameters and outputs resident in a device arena, cuts it into fixed
  * chunks and runs chunks of all admitted requests together in waves (one
@@ -477,7 +478,7 @@ void aeb_serve_destroy(aeb_server *srv);
 
 /*
  * aeb_ttc_sweep -- collision probability against the TTC trigger threshold
- * (SURVEY row a10; TTC = H0 / v_rel, Sec. VI-C).  Samples n_per_scenario
+ * (TTC = H0 / v_rel, Sec. VI-C).  Samples n_per_scenario
  * parameter sets of every scenario once on the host (Sec. IV-C), keeps them
  * resident, and runs every (threshold, scenario) pair as a job of batched
  * launches (thresholds in chunks, all reading the same parameter rows) with
