@@ -14,6 +14,7 @@
 // on every call.  The work is a single pass over 21 bytes per sample
 // (status, x_ref, v_imp, n_steps): bound by HBM bandwidth.
 #include <cfloat>
+#include <cmath>
 
 #include "aeb_internal.h"
 
@@ -23,14 +24,28 @@ namespace {
 constexpr int kRedThreads = 256;
 constexpr int kRedWarps = kRedThreads / 32;
 
-__device__ __forceinline__ int bin_index(double x, double lo, double inv_w)
+// floor((x - lo) / w) clamped to [0, NBINS - 1] for the power-of-two width
+// w = 2^-k.  (x - lo) is one binary64 subtraction, as in the definition; the
+// exact scaling by 2^k and the floor are done on its bits with integer
+// instructions, which keeps the binary64 pipe (1/64 rate on GB300) for the
+// sums.  y = m 2^ex with the 53-bit significand m, so floor(y 2^k) is m shifted
+// right by -(ex + k); a normal y with ex + k >= -40 is already >= 2^12.
+__device__ __forceinline__ int bin_index(double x, double lo, int k)
 {
-    // floor((x - lo) / w) for a power-of-two width w: (x - lo) * (1 / w) is the
-    // same exact scaling, so the bin equals the division-based definition.
-    const double q = floor((x - lo) * inv_w);
-    if (!(q >= 0.0)) return 0;
-    if (q > (double)(AEB_NBINS - 1)) return AEB_NBINS - 1;
-    return (int)q;
+    const long long b = __double_as_longlong(x - lo);
+    if (b <= 0) return 0;  // +0, or negative (sign bit set)
+    const int e = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = (unsigned long long)b & 0xfffffffffffffull;
+    int ex = -1074;        // subnormal: y = m 2^-1074
+    if (e != 0) {
+        m |= 1ull << 52;
+        ex = e - 1075;
+    }
+    const int sh = ex + k;
+    if (sh >= -40) return AEB_NBINS - 1;
+    const int r = -sh;
+    const unsigned long long q = (r >= 64) ? 0ull : (m >> r);
+    return q > (unsigned long long)(AEB_NBINS - 1) ? AEB_NBINS - 1 : (int)q;
 }
 
 __device__ __forceinline__ void init_partial(RedPartial &a)
@@ -108,7 +123,7 @@ __global__ void __launch_bounds__(kRedThreads)
 k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
                  const double *__restrict__ vi, const int32_t *__restrict__ ns, uint64_t n,
                  uint64_t chunk, const TileDesc *__restrict__ table, const JobDev *__restrict__ jobs,
-                 double lo_d, double inv_wd, double lo_v, double inv_wv,
+                 double lo_d, int k_d, double lo_v, int k_v,
                  RedPartial *__restrict__ part, unsigned long long *__restrict__ hist_d,
                  unsigned long long *__restrict__ hist_v)
 {
@@ -144,7 +159,7 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
             acc.sumsq_d += d * d;
             acc.min_d = fmin(acc.min_d, d);
             acc.max_d = fmax(acc.max_d, d);
-            if (HIST) atomicAdd(&sh_d[bin_index(d, lo_d, inv_wd)], 1u);
+            if (HIST) atomicAdd(&sh_d[bin_index(d, lo_d, k_d)], 1u);
         } else if (s == AEB_CONTACT) {
             const double v = vi[i];
             acc.n_contact++;
@@ -152,7 +167,7 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
             acc.sumsq_v += v * v;
             acc.min_v = fmin(acc.min_v, v);
             acc.max_v = fmax(acc.max_v, v);
-            if (HIST) atomicAdd(&sh_v[bin_index(v, lo_v, inv_wv)], 1u);
+            if (HIST) atomicAdd(&sh_v[bin_index(v, lo_v, k_v)], 1u);
         } else if (s == AEB_HORIZON) {
             acc.n_horizon++;
         } else {
@@ -250,8 +265,8 @@ cudaError_t launch_reduce(const uint8_t *status, const double *x_ref, const doub
     cudaError_t e = cudaMemsetAsync(stats->hist_d, 0, 2 * sizeof(uint64_t) * AEB_NBINS, s);
     if (e != cudaSuccess) return e;
     k_reduce_partial<true><<<g, kRedThreads, 0, s>>>(
-        status, x_ref, v_imp, n_steps, n, chunk, nullptr, nullptr, h.lo_d, 1.0 / h.w_d, h.lo_v,
-        1.0 / h.w_v, partials, reinterpret_cast<unsigned long long *>(stats->hist_d),
+        status, x_ref, v_imp, n_steps, n, chunk, nullptr, nullptr, h.lo_d, -std::ilogb(h.w_d),
+        h.lo_v, -std::ilogb(h.w_v), partials, reinterpret_cast<unsigned long long *>(stats->hist_d),
         reinterpret_cast<unsigned long long *>(stats->hist_v));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -266,7 +281,7 @@ cudaError_t launch_reduce_jobs(const uint8_t *status, const double *x_ref, const
 {
     if (n_blocks > 0) {
         k_reduce_partial<false><<<n_blocks, kRedThreads, 0, s>>>(
-            status, x_ref, v_imp, n_steps, 0, 0, blocks, jobs, 0.0, 1.0, 0.0, 1.0, partials,
+            status, x_ref, v_imp, n_steps, 0, 0, blocks, jobs, 0.0, 0, 0.0, 0, partials,
             nullptr, nullptr);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
