@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define AEB_ABI_VERSION 3
+#define AEB_ABI_VERSION 4
 #define AEB_NFIELDS 10   /* columns of a parameter set, see aeb_params       */
 #define AEB_NBINS 4096   /* bins of each fixed histogram in aeb_stats         */
 
@@ -182,12 +182,15 @@ typedef struct aeb_stats {
  * one persistent launch): its parameters are rows
  * [param_offset, param_offset + n) of the device columns, its outputs rows
  * [out_offset, out_offset + n) of the output columns; ttc_thr is its own TTC
- * threshold (used when model.trigger is AEB_TRIGGER_TTC). */
+ * threshold (used when model.trigger is AEB_TRIGGER_TTC); sample j of the job
+ * draws its per-step perception readings from row key_offset + j of the
+ * reading stream (a plain aeb_rollout uses the parameter row). */
 typedef struct aeb_job {
     uint64_t param_offset;
     uint64_t out_offset;
     uint64_t n;
     double ttc_thr;
+    uint64_t key_offset;
 } aeb_job;
 
 /* Per-job reduction of a batched launch: aeb_stats without the histograms. */

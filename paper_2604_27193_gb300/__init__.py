@@ -25,7 +25,7 @@ OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
 OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
               "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
               "n_onset": np.int32}
-ABI_VERSION = 3  # AEB_ABI_VERSION of include/aeb.h
+ABI_VERSION = 4  # AEB_ABI_VERSION of include/aeb.h
 NBINS = 4096
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)
@@ -83,7 +83,7 @@ class Stats(C.Structure):
 
 class Job(C.Structure):
     _fields_ = [("param_offset", C.c_uint64), ("out_offset", C.c_uint64), ("n", C.c_uint64),
-                ("ttc_thr", C.c_double)]
+                ("ttc_thr", C.c_double), ("key_offset", C.c_uint64)]
 
 
 class JobStats(C.Structure):
@@ -354,10 +354,12 @@ def aeb_evaluate(m, params_host: dict, n: int, precision: int, hist: HistSpec,
 
 
 def jobs_array(jobs) -> "C.Array":
-    """ctypes array of aeb_job from (param_offset, out_offset, n, ttc_thr) tuples."""
+    """ctypes array of aeb_job from (param_offset, out_offset, n, ttc_thr[,
+    key_offset]) tuples; key_offset defaults to param_offset."""
     arr = (Job * len(jobs))()
-    for k, (po, oo, n, thr) in enumerate(jobs):
-        arr[k] = Job(po, oo, n, thr)
+    for k, jb in enumerate(jobs):
+        po, oo, n, thr = jb[:4]
+        arr[k] = Job(po, oo, n, thr, jb[4] if len(jb) > 4 else po)
     return arr
 
 

@@ -45,6 +45,7 @@ struct OutDev {
 struct JobDev {
     uint64_t param_offset, out_offset, n;
     double ttc_thr;
+    uint64_t key_offset;  // row of the job's first sample in the perception stream
 };
 
 // A tile: `count` consecutive samples of job `job`, from its sample `first`.

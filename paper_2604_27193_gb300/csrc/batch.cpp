@@ -83,7 +83,7 @@ extern "C" aeb_status aeb_batch_create(const aeb_model *model, const aeb_job *jo
     for (uint32_t j = 0; j < n_jobs; ++j) {
         const aeb_job &jb = jobs[j];
         if (!std::isfinite(jb.ttc_thr)) return fail(AEB_EINVAL, "aeb_batch_create: ttc_thr not finite");
-        hj[j] = JobDev{jb.param_offset, jb.out_offset, jb.n, jb.ttc_thr};
+        hj[j] = JobDev{jb.param_offset, jb.out_offset, jb.n, jb.ttc_thr, jb.key_offset};
         for (uint64_t f = 0; f < jb.n; f += T)
             tiles.push_back(TileDesc{f, j, (uint32_t)std::min<uint64_t>(T, jb.n - f)});
         first[j] = (uint32_t)red.size();

@@ -20,7 +20,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
 // A claimed tile: `count` samples with parameters at rows p0.. and outputs at
 // rows o0.., and the TTC threshold of their job.  Warp-uniform.
 struct Tile {
-    uint64_t p0, o0;
+    uint64_t p0, o0, k0;  // parameter, output and perception-key rows of the first sample
     int count;
     double thr;
     bool ok;
@@ -36,19 +36,20 @@ __device__ __forceinline__ Tile claim_tile(const WorkDev &w, uint32_t tile_size,
     if (!w.tiles) {
         const uint64_t start = (uint64_t)t * tile_size;
         r.ok = start < w.n;
-        r.p0 = r.o0 = start;
+        r.p0 = r.o0 = r.k0 = start;
         r.count = r.ok ? (int)((w.n - start < (uint64_t)tile_size) ? w.n - start : tile_size) : 0;
         r.thr = model_thr;
     } else {
         r.ok = t < w.n_tiles;
         r.count = 0;
-        r.p0 = r.o0 = 0;
+        r.p0 = r.o0 = r.k0 = 0;
         r.thr = model_thr;
         if (r.ok) {
             const TileDesc d = w.tiles[t];
             const JobDev j = w.jobs[d.job];
             r.p0 = j.param_offset + d.first;
             r.o0 = j.out_offset + d.first;
+            r.k0 = j.key_offset + d.first;
             r.count = (int)d.count;
             r.thr = j.ttc_thr;
         }
@@ -75,7 +76,7 @@ struct WarpQueue {
 
     __device__ __forceinline__ bool take(unsigned need, const WorkDev &w, uint32_t tile_size,
                                          double model_thr, uint64_t &pidx, uint64_t &oidx,
-                                         double &thr)
+                                         uint64_t &kidx, double &thr)
     {
         const unsigned lane = threadIdx.x & 31u;
         bool mine = false;
@@ -94,6 +95,7 @@ struct WarpQueue {
                 mine = true;
                 pidx = cur.p0 + used + rank;
                 oidx = cur.o0 + used + rank;
+                kidx = cur.k0 + used + rank;
                 thr = cur.thr;
             }
             const unsigned taken = __ballot_sync(kFull, got);
@@ -176,7 +178,8 @@ __device__ __forceinline__ void load_fields(const ParamsDev &p, uint64_t i, doub
 namespace aeb {
 
 // The per-warp driver shared by both precisions.  `Lane` provides
-//   bool init(M, X, P, O, i)  -- load sample i; true if it already ended (stored)
+//   bool init(M, X, P, O, p, o, k, thr) -- load parameter row p (output row o,
+//                                perception key row k); true if it already ended
 //   bool step(M, X, P, O, i)  -- one RK4 step; true if the rollout ended (stored)
 // where X holds precision-specific constants (kernel parameters, so the
 // compiler reads them from the parameter bank rather than registers).
@@ -192,17 +195,17 @@ __device__ __forceinline__ void rollout_driver(const ModelDev &M, const X &Xc, c
     const unsigned lane = threadIdx.x & 31u;
     WarpQueue q;
     Lane L;
-    uint64_t pidx = 0, oidx = 0;
+    uint64_t pidx = 0, oidx = 0, kidx = 0;
     double thr = M.ttc_thr;
     bool active = false;
     unsigned need = kFull;
     for (;;) {
         while (need) {
-            const bool got = q.take(need, W, tile_size, M.ttc_thr, pidx, oidx, thr);
+            const bool got = q.take(need, W, tile_size, M.ttc_thr, pidx, oidx, kidx, thr);
             bool ended = false;
             if ((need >> lane) & 1u) {
                 active = got;
-                if (active) ended = L.init(M, Xc, P, O, pidx, oidx, thr);
+                if (active) ended = L.init(M, Xc, P, O, pidx, oidx, kidx, thr);
             }
             need = __ballot_sync(kFull, ended);
         }

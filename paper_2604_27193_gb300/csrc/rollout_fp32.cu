@@ -208,7 +208,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 enum {
     L_F0, L_F1, L_R0, L_R1, L_MG, L_GS, L_U, L_S, L_ETHK, L_NP1, L_NP2, L_NP3, L_NP4,  // floats
     L_SIGMA,
-    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI,                             // ints
+    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI, L_KIDXLO, L_KIDXHI,         // ints
     L_NW_BASE,
     L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NW_TTC  // TTC trigger only (floats)
 };
@@ -535,7 +535,9 @@ struct Lane32 {
         bool reading = true;
         float pn = 0.0f;
         if (F.perc) {
-            uint64_t c[4] = {pidx(), (uint64_t)((long long)n + F.plat), 0, 0};
+            const uint64_t krow = (uint64_t)(uint32_t)ci(L_KIDXLO) |
+                                  ((uint64_t)(uint32_t)ci(L_KIDXHI) << 32);
+            uint64_t c[4] = {krow, (uint64_t)((long long)n + F.plat), 0, 0};
             philox_block(c, F.pseed, kPercKey1);
             const float s24 = 5.9604644775390625e-8f;  // 2^-24
             const float u1 = (float)(uint32_t)(c[0] >> 40) * s24;
@@ -569,7 +571,7 @@ struct Lane32 {
     // Load sample `slot` of the warp's tile (parameter row pi, output row i);
     // true if it ended at once (stored).
     __device__ __forceinline__ bool init(const ModelDev &M, const ParamsDev &P, const OutDev &O,
-                                         uint64_t pi, uint64_t i, int slot, int T,
+                                         uint64_t pi, uint64_t i, uint64_t ki, int slot, int T,
                                          const float *tf, const int *ti)
     {
         const int kind = ti[R_KIND * T + slot];
@@ -614,6 +616,8 @@ struct Lane32 {
         set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
         set_ci(L_IDXLO, (int)(uint32_t)i);
         set_ci(L_IDXHI, (int)(uint32_t)(i >> 32));
+        set_ci(L_KIDXLO, (int)(uint32_t)ki);
+        set_ci(L_KIDXHI, (int)(uint32_t)(ki >> 32));
         if (TTC) {
             set_cf(L_NZ, tf[R_NZ * T + slot]);
             set_cf(L_THRH, tf[R_THRH * T + slot]);
@@ -804,7 +808,8 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 if (got) {
                     const int slot = cursor + (int)rank;
                     active = true;
-                    ended = L.init(M, P, O, tile.p0 + slot, tile.o0 + slot, slot, T, tf, ti);
+                    ended = L.init(M, P, O, tile.p0 + slot, tile.o0 + slot, tile.k0 + slot, slot,
+                                   T, tf, ti);
                 }
                 const unsigned taken = __ballot_sync(kFull, got);
                 cursor += __popc(taken);

@@ -53,7 +53,7 @@ struct Lane64 {
     double d0, gs, noise, k, it, thr;
     double mg, f0, f1, r0, r1, cap;
     double pa, pb, dlo, dhi;      // current line pa + pb D (piece 1, 2) and its interval
-    uint64_t row;                 // parameter row (counter of the perception readings)
+    uint64_t row;                 // perception key row (counter of the readings)
     int32_t n, n_b, n_delay;
     int piece;                    // 0: D, 1, 2: an axle line, 3: the constant cap; -1: none
     bool trig, lagged, ordered;
@@ -137,7 +137,8 @@ struct Lane64 {
     }
 
     __device__ __forceinline__ bool init(const ModelDev &M, const NoExtra &, const ParamsDev &P,
-                                         const OutDev &O, uint64_t pi, uint64_t i, double thr_job)
+                                         const OutDev &O, uint64_t pi, uint64_t i, uint64_t ki,
+                                         double thr_job)
     {
         double f[AEB_NFIELDS];
         load_fields(P, pi, f);
@@ -147,7 +148,7 @@ struct Lane64 {
             store_out(O, i, AEB_INVALID, nan, nan, nan, nan, 0, -1);
             return true;
         }
-        row = pi;
+        row = ki;
         d0 = f[kD0];
         gs = f[kGs];
         noise = f[kNoise];

@@ -292,7 +292,9 @@ bool aeb_server::launch_wave(Wave &w)
     for (uint32_t j = 0; j < nj; ++j) {
         const ChunkRef &c = w.chunks[j];
         const uint64_t row = c.req->row0 + c.first;
-        w.hjobs[j] = JobDev{row, row, c.n, model.ttc_thr};
+        // readings keyed by the sample's index in its request, so a request's
+        // results do not depend on where it sits in the arena
+        w.hjobs[j] = JobDev{row, row, c.n, model.ttc_thr, c.first};
         for (uint64_t f = 0; f < c.n; f += T)
             w.htiles[nt++] = TileDesc{f, j, (uint32_t)std::min<uint64_t>(T, c.n - f)};
         w.hfirst[j] = nr;

@@ -162,7 +162,7 @@ extern "C" aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *
         for (uint32_t t = 0; t < nt; ++t)
             for (uint32_t sc = 0; sc < n_scen; ++sc)
                 jobs.push_back(aeb_job{(uint64_t)sc * n_per, ((uint64_t)t * n_scen + sc) * n_per,
-                                       n_per, thresholds[t0 + t]});
+                                       n_per, thresholds[t0 + t], (uint64_t)sc * n_per});
         st = aeb_rollout_batched(&m, jobs.data(), (uint32_t)jobs.size(), &dp, precision, &out,
                                  static_cast<aeb_job_stats *>(dstats), stream);
         if (st != AEB_OK) break;

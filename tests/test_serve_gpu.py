@@ -149,3 +149,29 @@ def test_destroy_with_work_in_flight(aeb):
         srv.submit(ai.replace(sc, scenario_id=k), 200_000)
     time.sleep(0.01)
     srv.close()  # waits for the waves in flight, drops pending requests
+
+
+def test_perception_request_alone_equals_in_mix(aeb):
+    """With per-step perception the readings are keyed by a sample's index in
+    its request, so a request's statistics still do not depend on its company
+    or on where it lands in the arena."""
+    m = ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2, perc_latency=0.03,
+                   perc_seed=3)
+    srv = aeb.Server(m, aeb.FP32_COMP, arena_rows=1 << 21, chunk_samples=1 << 14,
+                     wave_samples=1 << 16, max_waves_in_flight=2, sampler_threads=8,
+                     max_request_samples=1 << 20)
+    try:
+        sc = ai.scenario_from_means(25.0, 0.4, 0.9, 60.0, seed=5, scenario_id=78)
+        code, alone, _ = srv.poll(srv.submit(sc, 200_000))
+        assert code == aeb.OK
+        reqs = ai.request_stream(rate=1000.0, duration=0.02, seed=9, n_lo=1e3, n_hi=2e5)
+        tickets = [srv.submit(s, n) for _, s, n in reqs[:8]]
+        tA = srv.submit(sc, 200_000)
+        tickets += [srv.submit(s, n) for _, s, n in reqs[8:16]]
+        code, mixed, _ = srv.poll(tA)
+        assert code == aeb.OK
+        assert same(alone, mixed), "a perception request's statistics changed with its company"
+        for tk in tickets:
+            assert srv.poll(tk)[0] == aeb.OK
+    finally:
+        srv.close()

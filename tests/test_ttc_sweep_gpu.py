@@ -65,3 +65,24 @@ def test_full_size_sweep(aeb, oracle_mod):
             pp = oracle_mod.sample(m, scen[s], 0, sub)
             ex = oracle_mod.reduce(oracle_mod.rollout(mt, pp))
             assert j64[t * 64 + s].n_contact == ex.n_contact and j64[t * 64 + s].steps == ex.steps
+
+
+def test_sweep_with_perception_fp64_against_oracle(aeb, oracle_mod):
+    """Per-step perception inside the batched sweep: a job's readings are keyed
+    by its parameter rows (scenario s occupies rows s n .. (s+1) n - 1 of the
+    shared block), so the binary64 counts equal the oracle's run on the same
+    rows."""
+    m = ai.replace(ai.ttc_model(), perc_sigma=0.6, perc_drop=0.15, perc_latency=0.02,
+                   perc_seed=5)
+    scen = ai.ttc_scenarios(4, seed=9)
+    thr = np.array([0.8, 1.6, 2.4])
+    n = 1500
+    res, jobs = aeb.aeb_ttc_sweep(m, scen, n, thr, aeb.FP64_PLAIN, per_job=True)
+    for t in range(len(thr)):
+        for s in range(len(scen)):
+            p = oracle_mod.sample(m, scen[s], 0, n)
+            ex = oracle_mod.reduce(oracle_mod.rollout(ai.replace(m, ttc_thr=float(thr[t])), p,
+                                                      threads=8, row0=s * n))
+            j = jobs[t * len(scen) + s]
+            assert (j.n_contact, j.n_stop, j.n_horizon, j.steps) == \
+                (ex.n_contact, ex.n_stop, ex.n_horizon, ex.steps), (t, s)
