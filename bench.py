@@ -543,6 +543,10 @@ def main():
            "api": "aeb_evaluate (pinned host params -> host stats)"}
 
     peaks = aeb.aeb_pipe_peaks(stream)
+    if rank != 0:  # the remaining lines are single-GPU measurements, taken by rank 0
+        if dist:
+            dist.destroy_process_group()
+        return
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
@@ -560,10 +564,6 @@ def main():
         torch.cuda.empty_cache()
         rare = rare_event_run(aeb, torch)
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -190,10 +190,11 @@ def is_estimate(weights, event):
 # Rollouts (Sec. III, IV-D, V-D)
 # --------------------------------------------------------------------------
 
-def rollout(model, params: dict, threads: int = 1) -> dict:
+def rollout(model, params: dict, threads: int = 1, row0: int = 0) -> dict:
     """Run every sample of ``params``; ``threads`` > 1 splits the samples into
     contiguous blocks handled by the same single-sample code in parallel (each
-    sample keeps its row index, which keys its perception readings)."""
+    sample keeps its row index, row0 + its position, which keys its
+    perception readings)."""
     n = len(params["v0"])
     out = {
         "status": np.empty(n, dtype=np.uint8),
@@ -210,7 +211,7 @@ def rollout(model, params: dict, threads: int = 1) -> dict:
     def run(lo: int, hi: int):
         arr, keep = _cols_array(params, lo)
         P = C.POINTER
-        L.om_rollout(C.byref(m), arr, lo, hi - lo,
+        L.om_rollout(C.byref(m), arr, row0 + lo, hi - lo,
                      C.cast(C.c_void_p(out["status"].ctypes.data + lo), P(C.c_uint8)),
                      *[C.cast(C.c_void_p(out[k].ctypes.data + 8 * lo), P(C.c_double))
                        for k in ("x_raw", "x_ref", "v_imp", "t_end")],
