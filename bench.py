@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--c1-full", action="store_true",
+                    help="run the binary64 kernel at every N x dt cell of the N sweep")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-grid and TTC-sweep lines")
     return ap.parse_args()
@@ -242,8 +244,67 @@ def sweep_run(aeb):
     dt = time.perf_counter() - t0
     total = sum(r.n for r in res)
     pick = {f"{r.threshold:.2f}": [r.p_contact, r.ci_lo, r.ci_hi] for r in res[::51]}
+    # per-threshold error against a binary64 rerun of a 1e6-sample subset (the first
+    # 61 samples of each scenario at every threshold; the binary64 counts equal the
+    # CPU oracle's, which the GPU tests check)
+    sub = 61
+    r64 = aeb.aeb_ttc_sweep(m, scen, sub, thr, aeb.FP64_PLAIN)
+    r32 = aeb.aeb_ttc_sweep(m, scen, sub, thr, aeb.FP32_COMP)
+    flips = [abs(a.n_contact - b.n_contact) for a, b in zip(r64, r32)]
     return {"rollouts": int(total), "seconds": dt, "rollouts_per_s": total / dt,
-            "p_contact_ci95_at": pick, "precision": "fp32-compensated"}
+            "p_contact_ci95_at": pick, "precision": "fp32-compensated",
+            "fp64_subset": {"rollouts": int(sum(r.n for r in r64)),
+                            "max_contact_count_diff_per_threshold": int(max(flips)),
+                            "thresholds_with_a_diff": int(sum(f > 0 for f in flips)),
+                            "max_abs_p_contact_err": max(abs(a.p_contact - b.p_contact)
+                                                         for a, b in zip(r64, r32))}}
+
+
+def c1_sweep(aeb, torch, full: bool):
+    """Throughput of both rollout kernels on the single-scenario workload at
+    N = 1e3 ... 1e7 samples and dt = 1 ms and 0.1 ms (the first N samples of one
+    seeded stream).  Per cell: CUDA-event time of one launch (mean of the timed
+    repeats after one warm-up launch) and rollouts/s.  The binary64 kernel runs
+    the cells of at most ~1e6 samples at 1 ms (~0.5 s each) unless ``full``;
+    its N = 1e7, 1 ms cell is the headline's binary64 arm."""
+    sizes = (1_000, 10_000, 100_000, 1_000_000, 10_000_000)
+    sc = ai.single_scenario(seed=0)
+    p = aeb.aeb_sample_params(ai.single_model(), sc, 0, sizes[-1])
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(sizes[-1], which=("status", "x_ref", "v_imp"))
+    del p
+
+    def timed(m, n, prec):
+        Pn = {f: P[f][:n] for f in ai.FIELDS}
+        On = {k: v[:n] for k, v in O.items()}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        aeb.aeb_rollout(m, Pn, n, prec, On)
+        e1.record()
+        torch.cuda.synchronize()
+        first = e0.elapsed_time(e1)
+        reps = 5 if first < 50 else (2 if first < 2000 else 1)
+        e0.record()
+        for _ in range(reps):
+            aeb.aeb_rollout(m, Pn, n, prec, On)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return {"ms": ms, "rollouts_per_s": n / (ms / 1e3), "repeats": reps}
+
+    cells = []
+    for dt in (1e-3, 1e-4):
+        m = ai.single_model(dt=dt)
+        for n in sizes:
+            c = {"dt_ms": dt * 1e3, "n": n, "fp32_comp": timed(m, n, aeb.FP32_COMP)}
+            if full or n * (1e-3 / dt) <= 1_000_000:
+                c["fp64_plain"] = timed(m, n, aeb.FP64_PLAIN)
+                c["fp32_over_fp64"] = c["fp32_comp"]["rollouts_per_s"] / c["fp64_plain"]["rollouts_per_s"]
+            cells.append(c)
+    del P, O
+    return {"workload": "single scenario (config-0 distributions), first N samples of one stream",
+            "timing": "one warm-up launch, then the mean of 1-5 launches (CUDA events)",
+            "cells": cells}
 
 
 def dt_study(aeb, torch):
@@ -550,13 +611,15 @@ def main():
     serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
     del P, O
     torch.cuda.empty_cache()
-    batched = sweep = dts = moving = percep = rare = None
+    batched = sweep = dts = moving = percep = rare = c1 = None
     if not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
         sweep = sweep_run(aeb)
         torch.cuda.empty_cache()
         dts = dt_study(aeb, torch)
+        torch.cuda.empty_cache()
+        c1 = c1_sweep(aeb, torch, args.c1_full)
         torch.cuda.empty_cache()
         moving = moving_lead_run(aeb, torch)
         torch.cuda.empty_cache()
@@ -600,6 +663,7 @@ def main():
         "batched_grid": batched,
         "ttc_sweep": sweep,
         "dt_study": dts,
+        "n_dt_sweep": c1,
         "moving_lead": moving,
         "perception": percep,
         "rare_event": rare,

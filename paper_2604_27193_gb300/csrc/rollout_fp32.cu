@@ -421,13 +421,19 @@ struct Lane32 {
         int len = room < AEB_FP32_WINDOW ? (int)room : AEB_FP32_WINDOW;
         if (TTC && !trig && tlen < len) len = tlen;
         if (e < cf(L_ETHK)) {  // close to a breakpoint (eth > 0 here)
+            // the largest k with e q^k >= m, from its binary digits: the
+            // window runs steps 0 .. k, so the crossing step comes next
             const float q = 1.0f + nmP, m = eth * kMargin;
             int lb = 1;
             if (q > 0.0f && q < 1.0f) {
-                const float q2 = q * q, q3 = q2 * q;
-                lb = (e * q >= m) ? 2 : 1;
-                if (e * q3 >= m) lb = 4;
-                if (AEB_FP32_WINDOW > 8 && e * (q3 * q3 * q) >= m) lb = 8;
+                const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
+                float r = e;
+                int k = 0;
+                if (r * q8 >= m) { r *= q8; k += 8; }
+                if (r * q4 >= m) { r *= q4; k += 4; }
+                if (r * q2 >= m) { r *= q2; k += 2; }
+                if (r * q >= m) k += 1;
+                lb = k + 1;
             }
             len = len < lb ? len : lb;
         }

@@ -205,6 +205,14 @@ FP32_CASES = {
                                    ttc_thr=3.0), ai.lead_braking_scenario(seed=20), 10_000),
     "ttc_perception": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2,
                                   perc_latency=0.05, perc_seed=13), ai.single_scenario(seed=23), 10_000),
+    # long approaches to the breakpoints of r(D): windows cut to the exact safe length
+    "per_axle_no_lead_slow_actuator": (ai.replace(ai.single_model(), lead=0),
+                                       ai.replace(ai.single_scenario(seed=24),
+                                                  tau=ai.uniform(0.3, 0.8)), 10_000),
+    "lumped_lead": (ai.replace(ai.single_model(), cap_mode=ai.CAP_LUMPED),
+                    ai.single_scenario(seed=25), 10_000),
+    # per-step actuator decay dt/tau up to 0.2
+    "coarse_dt_20ms": (ai.single_model(dt=0.02), ai.single_scenario(seed=26), 10_000),
 }
 
 
