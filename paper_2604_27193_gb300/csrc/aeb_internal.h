@@ -65,6 +65,7 @@ struct WorkDev {
     const TileDesc *tiles;
     uint64_t n_tiles;
     const JobDev *jobs;
+    uint64_t key_base;  // flat launches: perception-key row of sample 0
 };
 
 struct LaunchCfg {

@@ -149,7 +149,7 @@ extern "C" aeb_status aeb_batch_create(const aeb_model *model, const aeb_job *jo
     if (e == cudaSuccess) {
         cudaError_t le = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), cs);
         if (le == cudaSuccess && !tiles.empty()) {
-            WorkDev w{total, T, counter, dtiles, (uint64_t)tiles.size(), djobs};
+            WorkDev w{total, T, counter, dtiles, (uint64_t)tiles.size(), djobs, 0};
             le = (precision == AEB_FP64_PLAIN) ? launch_rollout_fp64(md, pd, od, w, cfg, cs)
                                                : launch_rollout_fp32(md, pd, od, w, cfg, cs);
         }

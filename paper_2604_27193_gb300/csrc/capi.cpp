@@ -202,7 +202,8 @@ std::mutex g_cfg_mu;
 LaunchCfg g_cfg[2] = {{128, 0, 256}, {128, 0, 32}};
 
 aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
-                        aeb_precision precision, const OutDev &od, cudaStream_t s)
+                        aeb_precision precision, const OutDev &od, cudaStream_t s,
+                        uint64_t key_base)
 {
     void *scratch = nullptr;
     aeb_status st = scratch_for(s, kCounterBytes + partial_bytes(), &scratch);
@@ -211,7 +212,7 @@ aeb_status rollout_impl(const ModelDev &md, const ParamsDev &pd, uint64_t n,
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
     const LaunchCfg cfg = launch_cfg(precision);
-    WorkDev w{n, (uint32_t)cfg.tile, counter, nullptr, 0, nullptr};
+    WorkDev w{n, (uint32_t)cfg.tile, counter, nullptr, 0, nullptr, key_base};
     e = (precision == AEB_FP64_PLAIN) ? launch_rollout_fp64(md, pd, od, w, cfg, s)
                                       : launch_rollout_fp32(md, pd, od, w, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -235,9 +236,14 @@ aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &
 // stream).  The parameter upload is cut into chunks: chunk k is copied on
 // `copy` while chunk k - 1 rolls out on comp[(k - 1) % 2], so the copies hide
 // behind the arithmetic, and two compute streams let a chunk's launch start
-// while the previous one drains its last rollouts.
+// while the previous one drains its last rollouts.  The first chunk is small,
+// so the arithmetic starts after a short upload; each later one is kEvalGrow
+// times the one before (an upload moves 80 B per sample, far faster than a
+// rollout of the sample, so a chunk's copy ends well before the previous
+// chunk's arithmetic), which keeps the launches, and their tails, few.
 constexpr int kEvalMaxChunks = 8;
-constexpr uint64_t kEvalMinChunk = uint64_t(1) << 20;
+constexpr uint64_t kEvalFirstChunk = uint64_t(1) << 18;
+constexpr uint64_t kEvalGrow = 6;
 struct EvalBuffers {
     void *base = nullptr;
     uint64_t cap = 0;  // samples
@@ -310,7 +316,7 @@ extern "C" aeb_status aeb_rollout(const aeb_model *model, const aeb_params *para
     if (precision != AEB_FP64_PLAIN && precision != AEB_FP32_COMP)
         return fail(AEB_EINVAL, "unknown precision");
     if (n == 0) return AEB_OK;
-    return rollout_impl(md, pd, n, precision, out_dev(out), static_cast<cudaStream_t>(stream));
+    return rollout_impl(md, pd, n, precision, out_dev(out), static_cast<cudaStream_t>(stream), 0);
 }
 
 extern "C" aeb_status aeb_reduce(const aeb_outputs *out, uint64_t n, const aeb_hist_spec *hist,
@@ -424,15 +430,24 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
         if (!host_out || !host_out->t_end) want.t_end = nullptr;
         if (!host_out || !host_out->n_onset) want.n_onset = nullptr;
         const OutDev od = out_dev(&want);
-        uint64_t chunks = (n + kEvalMinChunk - 1) / kEvalMinChunk;
-        if (chunks > (uint64_t)kEvalMaxChunks) chunks = kEvalMaxChunks;
-        const uint64_t per = (n + chunks - 1) / chunks;
+        // chunk boundaries: lengths kEvalFirstChunk, kEvalGrow times that, ...;
+        // the chunk whose length reaches the rest takes the rest (one chunk up
+        // to 2 kEvalFirstChunk samples)
+        uint64_t bound[kEvalMaxChunks + 1] = {0};
+        int chunks = 0;
+        for (uint64_t len = kEvalFirstChunk; bound[chunks] < n; len *= kEvalGrow) {
+            const uint64_t rest = n - bound[chunks];
+            const bool last = chunks == kEvalMaxChunks - 1 || rest <= len ||
+                              (chunks == 0 && rest <= 2 * kEvalFirstChunk);
+            bound[chunks + 1] = bound[chunks] + (last ? rest : len);
+            ++chunks;
+        }
         // the copies start after the work already queued on the caller's stream
         e = cudaEventRecord(eb->start, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(eb->copy, eb->start, 0);
         if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: stream order");
-        for (uint64_t k = 0; k < chunks; ++k) {
-            const uint64_t off = k * per, len = (off + per <= n) ? per : n - off;
+        for (int k = 0; k < chunks; ++k) {
+            const uint64_t off = bound[k], len = bound[k + 1] - bound[k];
             ParamsDev pk = pd;
             for (int j = 0; j < AEB_NFIELDS; ++j) {
                 e = cudaMemcpyAsync(const_cast<double *>(pd.col[j]) + off, hp.col[j] + off, 8 * len,
@@ -444,7 +459,7 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
             e = cudaEventRecord(eb->copied[k], eb->copy);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, eb->copied[k], 0);
             if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: chunk order");
-            st = rollout_impl(md, pk, len, precision, offset_out(od, off), cs);
+            st = rollout_impl(md, pk, len, precision, offset_out(od, off), cs, off);
             if (st != AEB_OK) return st;
         }
         for (int i = 0; i < 2; ++i) {

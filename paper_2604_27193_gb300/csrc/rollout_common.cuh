@@ -36,7 +36,8 @@ __device__ __forceinline__ Tile claim_tile(const WorkDev &w, uint32_t tile_size,
     if (!w.tiles) {
         const uint64_t start = (uint64_t)t * tile_size;
         r.ok = start < w.n;
-        r.p0 = r.o0 = r.k0 = start;
+        r.p0 = r.o0 = start;
+        r.k0 = w.key_base + start;
         r.count = r.ok ? (int)((w.n - start < (uint64_t)tile_size) ? w.n - start : tile_size) : 0;
         r.thr = model_thr;
     } else {

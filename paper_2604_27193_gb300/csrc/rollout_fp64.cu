@@ -29,6 +29,35 @@ namespace {
 
 __device__ __forceinline__ double dmin(double a, double b) { return (b < a) ? b : a; }
 
+// The per-step comparisons as integer comparisons of the bit patterns (the
+// binary64 pipe is the narrow one here): each gives the same truth value as
+// the binary64 comparison it replaces.
+
+// x <= 0.0 (false for a NaN).
+__device__ __forceinline__ bool le_zero(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned mag = (unsigned)hi & 0x7fffffffu;
+    const bool nan = mag > 0x7ff00000u || (mag == 0x7ff00000u && lo != 0);
+    return !nan && (hi < 0 || (mag | (unsigned)lo) == 0u);
+}
+
+// x >= y for a finite y > 0 (false for a NaN x): non-negative doubles order
+// as their bit patterns, and every negative x (-0 included) has the sign bit.
+__device__ __forceinline__ bool ge_pos(double x, double y)
+{
+    const long long bx = __double_as_longlong(x), by = __double_as_longlong(y);
+    return bx >= by && bx <= 0x7ff0000000000000ll;
+}
+
+// Order key of a non-NaN double: a signed integer that increases with the
+// value and is equal for -0 and +0; okey(-x) = -okey(x).
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 ? -(b & 0x7fffffffffffffffll) : b;
+}
+
 struct NoExtra {};
 
 __device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000ll); }
@@ -52,7 +81,8 @@ struct Lane64 {
     double x, v, a;
     double d0, gs, noise, k, it, thr;
     double mg, f0, f1, r0, r1, cap;
-    double pa, pb, dlo, dhi;      // current line pa + pb D (piece 1, 2) and its interval
+    double pa, pb;                // current line pa + pb D (piece 1, 2)
+    long long klo, khi;           // its demand interval [dlo, dhi] as order keys
     uint64_t row;                 // perception key row (counter of the readings)
     int32_t n, n_b, n_delay;
     int piece;                    // 0: D, 1, 2: an axle line, 3: the constant cap; -1: none
@@ -92,8 +122,8 @@ struct Lane64 {
             else lo = fmax(lo, B + band);
         }
         if (!(lo <= D && D <= hi)) return;
-        dlo = lo;
-        dhi = hi;
+        klo = okey(lo);
+        khi = okey(hi);
         if (CAP == AEB_CAP_LUMPED) {
             piece = (cur == 0) ? 0 : 3;
         } else {
@@ -240,9 +270,11 @@ struct Lane64 {
         // fourth (-a1 smallest when the command is a deceleration, so that
         // a - u >= 0 from the start, -a4 smallest otherwise): two tests for
         // the step.
+        // (A piece exists only when dt / tau <= 2, where the lag is stable and
+        // the stage actuator values are finite, so order keys compare them.)
         const bool dec = M.a_cmd <= 0.0;
-        const double dfirst = dec ? -a1 : -a4, dlast = dec ? -a4 : -a1;
-        const bool pw = piece >= 0 && dfirst >= dlo && dlast <= dhi;
+        const long long kfirst = -okey(dec ? a1 : a4), klast = -okey(dec ? a4 : a1);
+        const bool pw = piece >= 0 && kfirst >= klo && klast <= khi;
         const bool lines = __any_sync(__activemask(), pw && (piece == 1 || piece == 2));
         double kv1, kv2, kv3, kv4, v2, v3, v4;
         if (pw) {
@@ -278,13 +310,13 @@ struct Lane64 {
                           ((double)n + s) * dt, n + 1, onset());
                 return true;
             }
-        } else if (LEAD && xn >= d0) {
+        } else if (LEAD && ge_pos(xn, d0)) {  // d0 > 0 and finite here
             const double s = (d0 - x) / (xn - x);
             store_out(O, i, AEB_CONTACT, xn, d0, v + s * (vn - v), ((double)n + s) * dt, n + 1,
                       onset());
             return true;
         }
-        if (vn <= 0.0) {
+        if (le_zero(vn)) {
             const double s = v / (v - vn);
             store_out(O, i, AEB_STOP, xn, x + s * (xn - x), 0.0, ((double)n + s) * dt, n + 1,
                       onset());

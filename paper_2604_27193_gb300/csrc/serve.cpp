@@ -319,7 +319,7 @@ bool aeb_server::launch_wave(Wave &w)
         od.x_ref = dxref;
         od.v_imp = dvimp;
         od.n_steps = dnsteps;
-        WorkDev wd{total, T, w.counter, w.dtiles, nt, w.djobs};
+        WorkDev wd{total, T, w.counter, w.dtiles, nt, w.djobs, 0};
         e = (cfg.precision == AEB_FP64_PLAIN) ? launch_rollout_fp64(md, pd, od, wd, lcfg, w.stream)
                                               : launch_rollout_fp32(md, pd, od, wd, lcfg, w.stream);
     }

@@ -295,12 +295,14 @@ def test_evaluate_host_path(aeb, oracle_mod):
     assert bytes(st2) == bytes(st)
 
 
-def test_evaluate_chunked_upload(aeb):
-    """aeb_evaluate above 2^20 samples uploads and rolls out in chunks on
-    internal streams; its outputs and statistics are byte-identical to one
-    device-resident rollout and reduction of the same parameters."""
+@pytest.mark.parametrize("n", [2_500_003, 10_000_000])
+def test_evaluate_chunked_upload(aeb, n):
+    """aeb_evaluate above 2^19 samples uploads and rolls out in chunks of
+    growing length on internal streams (2.5e6: three chunks, the last shorter
+    than the one before; 1e7: the benchmark's end-to-end call); its outputs and
+    statistics are byte-identical to one device-resident rollout and reduction
+    of the same parameters."""
     m = ai.single_model()
-    n = 2_500_003  # three chunks, ragged last one
     p = aeb.aeb_sample_params(m, ai.single_scenario(seed=41), 0, n)
     which = ("status", "x_ref", "v_imp", "n_steps", "n_onset")
     host_out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in which}
@@ -308,6 +310,28 @@ def test_evaluate_chunked_upload(aeb):
     P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
     O = aeb.alloc_outputs(n, which=which)
     aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+    S = aeb.alloc_stats()
+    aeb.aeb_reduce(O, n, aeb.hist_spec(), S)
+    for k in which:
+        assert np.array_equal(host_out[k].view(np.uint8), O[k].cpu().numpy().view(np.uint8)), k
+    assert bytes(st) == bytes(S.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_evaluate_chunked_perception_keys(aeb, precision):
+    """Per-step perception readings are keyed by the sample's row in the
+    whole call: through aeb_evaluate's chunks (here two, the second starting at
+    row 262,144) every output equals one flat aeb_rollout of the same rows."""
+    m = ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2, perc_latency=0.05,
+                   perc_seed=13)
+    n = 600_001
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=43), 0, n)
+    which = ("status", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
+    host_out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in which}
+    st = aeb.aeb_evaluate(m, p, n, precision, aeb.hist_spec(), host_out=host_out)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n, which=which)
+    aeb.aeb_rollout(m, P, n, precision, O)
     S = aeb.alloc_stats()
     aeb.aeb_reduce(O, n, aeb.hist_spec(), S)
     for k in which:
