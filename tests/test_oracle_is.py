@@ -102,3 +102,27 @@ def test_incompatible_proposal_rejected(oracle_mod):
         oracle_mod.sample_is(ai.paper_model(), p, ai.replace(q, mass=ai.uniform(1400.0, 1700.0)), 0, 10)
     with pytest.raises(ValueError):
         oracle_mod.sample_is(ai.paper_model(), p, ai.replace(q, v0=ai.normal(34.0, 2.5, 21.0, 38.0)), 0, 10)
+
+
+def test_is_standard_error(oracle_mod):
+    """The reported standard error is that of the mean of y = w 1[E]: equal to
+    numpy's sample variance (ddof = 1) over n, and calibrated: over 200
+    independent batches of the rare event above, the spread of the estimates
+    matches the mean reported standard error, and the 95 % intervals cover the
+    exact probability about 95 % of the time."""
+    p = ai.Scenario(v0=ai.normal(30.0, 2.0), seed=3)
+    q = ai.replace(p, v0=ai.normal(36.0, 2.0), scenario_id=1)
+    n, batches = 2_000, 200
+    exact = stats.norm.sf(3.0)
+    est, ses, cover = [], [], 0
+    for b in range(batches):
+        cols, w = oracle_mod.sample_is(ai.paper_model(), p, q, b * n, n)
+        e, se, (lo, hi) = oracle_mod.is_estimate(w, cols["v0"] > 36.0)
+        y = np.where(cols["v0"] > 36.0, w, 0.0)
+        assert abs(se - math.sqrt(np.var(y, ddof=1) / n)) <= 1e-12 * se
+        est.append(e)
+        ses.append(se)
+        cover += lo <= exact <= hi
+    spread = np.std(est, ddof=1)
+    assert abs(spread / np.mean(ses) - 1.0) < 0.2, (spread, np.mean(ses))
+    assert 0.88 * batches <= cover <= 0.995 * batches, cover

@@ -1,8 +1,11 @@
 """The oracle's pins must catch plausible mistakes.  Each case plants one
 mistake in a copy of the oracle source (on the CPU, in a temporary directory),
 builds it, and runs the oracle pin tests against that build in a child
-process: at least one pin has to fail."""
+process: at least one pin has to fail.  The C cases mutate the C oracle; the
+Python cases mutate the package's own statistics (interval, quantile,
+exceedance, importance-sampling estimate)."""
 import os
+import shutil
 import subprocess
 import sys
 
@@ -50,7 +53,36 @@ MUTATIONS = [
     ("IS uniform ratio inverted", "return (q->p1 - q->p0) / (p->p1 - p->p0);",
      "return (p->p1 - p->p0) / (q->p1 - q->p0);"),
     ("IS atom ignored", "if (mq > 0.0) return cdf_dist(p, p->lo) / mq;", "if (mq < 0.0) return 1.0;"),
+    ("rear axle static share", "c->r0 = (c->mg * (1.0 - m->phi_f)) / (1.0 + mh);",
+     "c->r0 = (c->mg * m->phi_f) / (1.0 + mh);"),
+    ("rear brake share", "c->r1 = m->beta / (1.0 + mh);", "c->r1 = (1.0 - m->beta) / (1.0 + mh);"),
+    ("drag constant", "c->k = ((m->rho * cd) * m->area) / (2.0 * mass);",
+     "c->k = ((m->rho * cd) * m->area) / mass;"),
+    ("actuator rate", "c->it = (tau > 0.0) ? 1.0 / tau : 0.0;", "c->it = (tau > 0.0) ? tau : 0.0;"),
+    ("horizon step", "if (n + 1 >= n_max) {", "if (n + 2 >= n_max) {"),
+    ("second moment", "st->sumsq_d += d * d;", "st->sumsq_d += d;"),
+    ("clamp upper bound", "if (x > d->hi) x = d->hi;", "if (x > d->hi) x = d->lo;"),
+    ("normal scale", "x = d->p0 + d->p1 * z;", "x = d->p0 + z;"),
 ]
+
+
+PY_MUTATIONS = [
+    ("Wilson centre", "centre = (p + z * z / (2.0 * n)) / den", "centre = p / den"),
+    ("quantile index", "k = int(np.ceil(q * len(s)))", "k = int(np.floor(q * len(s)))"),
+    ("exceedance at the headway", "np.asarray(values) > h", "np.asarray(values) >= h"),
+    ("IS variance centring", "var = (math.fsum(y * y) - n * p * p) / (n - 1)",
+     "var = math.fsum(y * y) / (n - 1)"),
+]
+
+PIN_TESTS = ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py",
+             "test_oracle_perception.py", "test_oracle_is.py")
+
+
+def run_pins(env):
+    tests = [os.path.join(ROOT, "tests", f) for f in PIN_TESTS]
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           *tests], cwd=ROOT, env=env, capture_output=True, text=True,
+                          timeout=600)
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
@@ -62,10 +94,18 @@ def test_planted_mistake_is_caught(tmp_path, name, old, new):
     so = tmp_path / "m.so"
     subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o",
                     str(so), str(mutated), "-lm"], check=True)
-    env = dict(os.environ, AEB_ORACLE_SO=str(so))
-    tests = [os.path.join(ROOT, "tests", f) for f in
-             ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py",
-              "test_oracle_perception.py", "test_oracle_is.py")]
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        *tests], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    r = run_pins(dict(os.environ, AEB_ORACLE_SO=str(so)))
+    assert r.returncode == 1, f"mutation '{name}' survived:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name,old,new", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_planted_python_mistake_is_caught(tmp_path, oracle_mod, name, old, new):
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    shutil.copy(SRC, pkg / "aeb_oracle.c")
+    py = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    assert py.count(old) == 1, f"mutation anchor not unique: {old}"
+    (pkg / "__init__.py").write_text(py.replace(old, new))
+    env = dict(os.environ, AEB_ORACLE_PKG_ROOT=str(tmp_path), AEB_ORACLE_SO=oracle_mod.build())
+    r = run_pins(env)
     assert r.returncode == 1, f"mutation '{name}' survived:\n{r.stdout[-2000:]}"
