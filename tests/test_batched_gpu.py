@@ -182,3 +182,54 @@ def test_autotune_and_cache(aeb, tmp_path):
             assert torch.equal(ref[k], O[k]), k
     finally:
         aeb.aeb_set_launch_config(aeb.FP32_COMP, old.tile, old.blocks_per_sm)
+
+
+def test_full_grid_sampled(aeb, oracle_mod):
+    """The full scenario grid in the benchmark's configuration (4,096 scenarios,
+    N log-uniform in [1e3, 6.4e4], ~6.3e7 rollouts, one captured plan):
+    every job's counts add up; sampled samples of 16 jobs against the binary64
+    oracle within the FP32 tolerance; three whole jobs identical to flat
+    launches of their rows."""
+    m = ai.single_model()
+    grid = ai.grid_scenarios(seed=2)
+    total = sum(n for _, n in grid)
+    host = {f: np.empty(total, dtype=np.float64) for f in ai.FIELDS}
+    jobs, off = [], 0
+    for sc, n in grid:
+        aeb.aeb_sample_params(m, sc, 0, n, {f: host[f][off:off + n] for f in ai.FIELDS})
+        jobs.append((off, off, n, 0.0))
+        off += n
+    P = to_dev(host)
+    which = ("status", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
+    O = aeb.alloc_outputs(total, which=which)
+    S = torch.empty(aeb.JOB_STATS_BYTES * len(jobs), dtype=torch.uint8, device="cuda")
+    plan = aeb.BatchPlan(m, jobs, P, aeb.FP32_COMP, O, S)
+    plan.run()
+    torch.cuda.synchronize()
+    plan.close()
+    st = aeb.job_stats_from_buffer(S, len(jobs))
+    assert len(st) == 4096 and sum(s.n for s in st) == total
+    for s, (_, _, n, _) in zip(st, jobs):
+        assert s.n == n and s.n_stop + s.n_contact + s.n_horizon + s.n_invalid == n
+    out = {k: v.cpu().numpy() for k, v in O.items()}
+    rng = np.random.default_rng(11)
+    for j in rng.choice(len(jobs), 16, replace=False):
+        po, oo, n, _ = jobs[j]
+        rows = np.sort(rng.choice(n, min(n, 48), replace=False))
+        p = {f: host[f][po + rows] for f in ai.FIELDS}
+        exp = oracle_mod.rollout(m, p)
+        got = {k: out[k][oo + rows] for k in which}
+        same = got["status"] == exp["status"]
+        gap = p["d0"] - np.where(same, exp["x_ref"], np.minimum(exp["x_ref"], got["x_ref"]))
+        assert np.all(same | (np.abs(gap) < 1e-3)), j
+        stp = same & (exp["status"] == 0)
+        rel = np.abs(got["x_ref"][stp] - exp["x_ref"][stp]) / exp["x_ref"][stp]
+        assert rel.size == 0 or rel.max() <= 1e-5, (j, rel.max())
+        assert np.array_equal(got["n_onset"], exp["n_onset"])
+    for j in (0, 2047, 4095):
+        po, oo, n, _ = jobs[j]
+        Pj = {f: P[f][po:po + n].contiguous() for f in ai.FIELDS}
+        Oj = aeb.alloc_outputs(n, which=which)
+        aeb.aeb_rollout(m, Pj, n, aeb.FP32_COMP, Oj)
+        for k in which:
+            assert np.array_equal(bits(Oj[k].cpu().numpy()), bits(out[k][oo:oo + n])), (j, k)

@@ -142,6 +142,44 @@ def test_rk4_fourth_order_convergence(oracle_mod):
 # Contact with a stationary lead at d0
 # ---------------------------------------------------------------------------
 
+def _rk4_linear_step(M, c, z, h):
+    """One classic RK4 step of z' = M z + c, written as what it is for a linear
+    system: z + h sum_{j=0..3} (hM)^j / (j+1)! (M z + c), the degree-4 Taylor
+    polynomial of the exact flow (the textbook stability function of RK4)."""
+    def mv(A, x):
+        return [sum(A[i][k] * x[k] for k in range(3)) for i in range(3)]
+    f = [a + b for a, b in zip(mv(M, z), c)]
+    term, acc = f, list(f)
+    for j in range(1, 4):
+        term = [h * t / (j + 1) for t in mv(M, term)]
+        acc = [a + t for a, t in zip(acc, term)]
+    return [zi + h * ai_ for zi, ai_ in zip(z, acc)]
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_rk4_steps_against_exact_rationals(oracle_mod, steps):
+    """Hand-stepped case: no drag, flat road, a cap far above the demand and an
+    immediate command, so (x, v, a) follows the linear system x' = v, v' = a,
+    a' = (a_cmd - a) / tau.  After 1, 2, 3 steps of dt = 20 ms at tau = 50 ms
+    (dt / tau = 0.4, so every RK4 coefficient matters well above rounding) the
+    oracle's position equals the exact rational RK4 iterate (Python fractions,
+    from the binary64 inputs) to 1e-14 relative."""
+    from fractions import Fraction as Fr
+    dt, tau, acmd, v0 = 0.02, 0.05, -6.0, 20.0
+    m = ai.replace(ai.paper_model(), dt=dt, t_max=steps * dt, a_cmd=acmd)
+    p = one([v0, 100.0, 1.2, 0.0, 1500.0, 0.0, tau, 0.0, 0.0])
+    out = oracle_mod.rollout(m, p)
+    assert out["status"][0] == 2 and out["n_steps"][0] == steps
+    it = Fr(1.0 / tau)  # the model's 1 / tau constant, as a binary64 value
+    M = [[Fr(0), Fr(1), Fr(0)], [Fr(0), Fr(0), Fr(1)], [Fr(0), Fr(0), -it]]
+    c = [Fr(0), Fr(0), it * Fr(acmd)]
+    z = [Fr(0), Fr(v0), Fr(0)]
+    for _ in range(steps):
+        z = _rk4_linear_step(M, c, z, Fr(dt))
+    x_exact = float(z[0])
+    assert abs(out["x_raw"][0] - x_exact) <= 1e-14 * abs(x_exact), (out["x_raw"][0], x_exact)
+
+
 @pytest.mark.parametrize("d0,delay", [(40.0, 0.2), (55.5, 0.05), (3.0, 0.3)])
 def test_contact_kinematics(oracle_mod, d0, delay):
     v0, mu = 30.0, 0.6
