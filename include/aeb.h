@@ -381,6 +381,14 @@ aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n, const aeb_hist
  *   params      HOST columns (pinned memory gives the fastest copies)
  *   host_stats  host aeb_stats written on success
  *   host_out    host columns for per-sample outputs, or NULL / NULL members
+ * Above 2^19 samples the upload is cut into chunks of growing length (2^18
+ * samples first, then six times the previous one), each rolled out as soon as
+ * it has arrived, on internal streams ordered after the work already queued
+ * on `stream`; results are the same bits as one aeb_rollout + aeb_reduce of
+ * all n samples (sample i keeps row i for its perception readings).
+ * The device buffers, internal streams and events are kept per (device,
+ * stream) and grown as needed until the process exits; calls on the same
+ * stream from several threads must be serialised by the caller.
  * Synchronous.  AEB_ENOMEM if the device buffers cannot be grown.
  */
 aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64_t n,
