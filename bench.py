@@ -608,11 +608,16 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate) if args.serve_seconds > 0 else None
+    # the serving run and the extra lines are single-GPU measurements: the N = 1
+    # line carries them, a multi-GPU line only its own sharded numbers
+    single = world == 1
+    serving = None
+    if single and args.serve_seconds > 0:
+        serving = serve_run(aeb, m, args.serve_seconds, args.serve_rate)
     del P, O
     torch.cuda.empty_cache()
     batched = sweep = dts = moving = percep = rare = c1 = None
-    if not args.no_extras:
+    if single and not args.no_extras:
         batched = batched_run(aeb, torch, dev, stream)
         torch.cuda.empty_cache()
         sweep = sweep_run(aeb)
@@ -674,7 +679,7 @@ def main():
         "stats": {"n_stop": int(st.n_stop), "n_contact": int(st.n_contact),
                   "n_horizon": int(st.n_horizon), "p_contact": st.n_contact / st.n},
     }
-    if not args.no_cpu_baseline:
+    if single and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, sc, args.cpu_sample)
     print(json.dumps(line))
     if dist:
