@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--ttc-thr", type=float, default=None,
+                    help="brake on the TTC trigger at this threshold (s) instead of "
+                         "immediately (same samples; for profiling the TTC kernel)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -462,9 +465,16 @@ def rare_event_run(aeb, torch):
             "precision": "fp32-compensated"}
 
 
+def model_of(args):
+    if args.ttc_thr is not None:
+        return ai.ttc_model(thr=args.ttc_thr, dt=args.dt)
+    return ai.single_model(dt=args.dt)
+
+
 def config(args, world):
+    trig = "immediate trigger" if args.ttc_thr is None else f"TTC trigger at {args.ttc_thr:g} s"
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
-                        "10 s horizon, lead at d0, per-axle caps, immediate trigger",
+                        f"10 s horizon, lead at d0, per-axle caps, {trig}",
             "n_samples_per_gpu": args.n, "dt_s": args.dt, "precision": "fp32-compensated",
             "l2": "inputs 800 MB per GPU > 129 MB L2, no flush",
             "parallelism": f"replicas x{world} (independent sample shards)"}
@@ -474,7 +484,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    m = ai.single_model(dt=args.dt)
+    m = model_of(args)
     sc = ai.single_scenario(seed=0)
     import oracle
     cores = os.cpu_count() or 1
@@ -514,7 +524,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     N = args.n
-    m = ai.single_model(dt=args.dt)
+    m = model_of(args)
     sc = ai.replace(ai.single_scenario(seed=0), scenario_id=rank)  # each rank its own shard
 
     # host sampling into pinned buffers, then resident device copies

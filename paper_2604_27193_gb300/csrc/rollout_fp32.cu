@@ -110,6 +110,12 @@ __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
 // threshold.
 constexpr float kMargin = 1.00001f;
 
+// Before its TTC trigger a lane tests the trigger only at steps where it could
+// fire: one test bounds how fast the trigger margin can fall over up to
+// kTtcSpan steps (speed bound over the span, see ttc_check) and sets the step
+// of the next test.
+constexpr int kTtcSpan = 512;
+
 // q^P by repeated squaring (P < 32, a compile-time constant).
 template <int P>
 __device__ __forceinline__ float powi(float q)
@@ -210,7 +216,7 @@ enum {
     L_SIGMA,
     L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI, L_KIDXLO, L_KIDXHI,         // ints
     L_NW_BASE,
-    L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NW_TTC  // TTC trigger only (floats)
+    L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NCHK, L_NW_TTC  // TTC trigger only (NCHK: int)
 };
 template <bool TTC>
 __host__ __device__ constexpr int cold_fields() { return TTC ? L_NW_TTC : L_NW_BASE; }
@@ -515,9 +521,11 @@ struct Lane32 {
 
     // TTC trigger (while not yet triggered): (g + noise) - thr v <= 0, with the
     // exact rounding error of thr * vh; braking starts n_delay steps later.
-    // Returns how many steps (1 .. K) may run before the next test: before
-    // the trigger the car coasts, the stage accelerations are q = w^2 + C >= C,
-    // so over a window the scaled speed stays below W = w + K s dt max(0, -C)
+    // Returns how many steps (1 .. kTtcSpan; whole windows from K up) may run
+    // before the next test:
+    // before the trigger the car coasts, the stage accelerations are
+    // q = w^2 + C >= C, so over the span the scaled speed stays below
+    // W = w + kTtcSpan s dt max(0, -C)
     // and the margin falls by at most 6 W + thr' s dt max(0, -C) per step
     // (the gap by the stage-speed sum, the speed term by the speed gain); the
     // first L - 1 steps after this one cannot trigger while (L - 1) times that
@@ -562,7 +570,7 @@ struct Lane32 {
             return AEB_FP32_WINDOW;
         }
         const float sdt = -ndts, acc = fmaxf(0.0f, -C);
-        const float W = fmaf((float)AEB_FP32_WINDOW * sdt, acc, vh + vl);
+        const float W = fmaf((float)kTtcSpan * sdt, acc, vh + vl);  // speed bound over the span
         // (a braking lead's speed term falls by thr' s dt b_L per step more;
         // its travel only widens the gap)
         const float d = fmaf(6.0f, W, thr_h * sdt * (acc + F.lb)) * 1.001f;
@@ -571,7 +579,10 @@ struct Lane32 {
         const float mw = F.perc ? fmaf(-3.0f * F.psig, cf(L_SIGMA), m) : m;
         const float r = __fdividef(mw, d) * 0.999f;
         if (!(r > 0.0f)) return 1;
-        return r >= (float)(AEB_FP32_WINDOW - 1) ? AEB_FP32_WINDOW : 1 + (int)r;
+        const int t = r >= (float)(kTtcSpan - 1) ? kTtcSpan : 1 + (int)r;
+        // a span of whole windows (testing earlier is always safe), so that
+        // far from the trigger the next test falls on a window boundary
+        return t >= AEB_FP32_WINDOW ? t - t % AEB_FP32_WINDOW : t;
     }
 
     // Load sample `slot` of the warp's tile (parameter row pi, output row i);
@@ -626,6 +637,7 @@ struct Lane32 {
         set_ci(L_KIDXHI, (int)(uint32_t)(ki >> 32));
         if (TTC) {
             set_cf(L_NZ, tf[R_NZ * T + slot]);
+            set_ci(L_NCHK, 0);  // test the trigger at the first step
             set_cf(L_THRH, tf[R_THRH * T + slot]);
             set_cf(L_THRL, tf[R_THRL * T + slot]);
         }
@@ -831,7 +843,13 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         bool ended = false;
         float vl1, gl1;  // end-of-step low words of a slow step that ended
         int tlen = AEB_FP32_WINDOW;  // steps before the next TTC test
-        if (TTC && active && !L.trig) tlen = L.ttc_check(F, n_last);
+        if (TTC && active && !L.trig) {
+            tlen = L.ci(L_NCHK) - L.n;  // steps the last test still covers
+            if (tlen <= 0) {
+                tlen = L.ttc_check(F, n_last);
+                if (!L.trig) L.set_ci(L_NCHK, L.n + tlen);
+            }
+        }
         // Most passes: every active lane can run a full window (no event in
         // reach); one vote decides.  Otherwise handle onsets, slow steps and
         // window lengths lane by lane.
