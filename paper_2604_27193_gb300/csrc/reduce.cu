@@ -12,7 +12,9 @@
 //   2. one block adds the G partials in the same fixed pattern.
 // G and chunk depend only on n, so the floating-point sums are the same bits
 // on every call.  The work is a single pass over 21 bytes per sample
-// (status, x_ref, v_imp, n_steps): bound by HBM bandwidth.
+// (status, x_ref, v_imp, n_steps); its time is set by the binary64 sums and
+// squares (1/64 rate on GB300), so the bin index and the extremes are taken
+// from the bits with integer instructions.
 #include <cfloat>
 #include <cmath>
 
@@ -46,6 +48,15 @@ __device__ __forceinline__ int bin_index(double x, double lo, int k)
     const int r = -sh;
     const unsigned long long q = (r >= 64) ? 0ull : (m >> r);
     return q > (unsigned long long)(AEB_NBINS - 1) ? AEB_NBINS - 1 : (int)q;
+}
+
+// Total-order key of a double (an involution): the bits for a non-negative
+// value, the magnitude bits flipped for a negative one, so that keys compare as
+// signed integers in the order of the values (-0 just below +0).  The thread
+// loop keeps its extremes as keys, on the integer pipe.
+__device__ __forceinline__ long long order_key(long long b)
+{
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
 __device__ __forceinline__ void init_partial(RedPartial &a)
@@ -149,24 +160,28 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
     }
     RedPartial acc;
     init_partial(acc);
+    long long kmin_d = order_key(0x7ff0000000000000ll), kmax_d = order_key(0xfff0000000000000ll);
+    long long kmin_v = kmin_d, kmax_v = kmax_d;
     for (uint64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
         const uint8_t s = st[i];
         acc.steps += (unsigned long long)(long long)ns[i];
         if (s == AEB_STOP) {
             const double d = xr[i];
+            const long long kd = order_key(__double_as_longlong(d));
             acc.n_stop++;
             acc.sum_d += d;
             acc.sumsq_d += d * d;
-            acc.min_d = fmin(acc.min_d, d);
-            acc.max_d = fmax(acc.max_d, d);
+            kmin_d = kd < kmin_d ? kd : kmin_d;
+            kmax_d = kd > kmax_d ? kd : kmax_d;
             if (HIST) atomicAdd(&sh_d[bin_index(d, lo_d, k_d)], 1u);
         } else if (s == AEB_CONTACT) {
             const double v = vi[i];
+            const long long kv = order_key(__double_as_longlong(v));
             acc.n_contact++;
             acc.sum_v += v;
             acc.sumsq_v += v * v;
-            acc.min_v = fmin(acc.min_v, v);
-            acc.max_v = fmax(acc.max_v, v);
+            kmin_v = kv < kmin_v ? kv : kmin_v;
+            kmax_v = kv > kmax_v ? kv : kmax_v;
             if (HIST) atomicAdd(&sh_v[bin_index(v, lo_v, k_v)], 1u);
         } else if (s == AEB_HORIZON) {
             acc.n_horizon++;
@@ -174,6 +189,10 @@ k_reduce_partial(const uint8_t *__restrict__ st, const double *__restrict__ xr,
             acc.n_invalid++;
         }
     }
+    acc.min_d = __longlong_as_double(order_key(kmin_d));
+    acc.max_d = __longlong_as_double(order_key(kmax_d));
+    acc.min_v = __longlong_as_double(order_key(kmin_v));
+    acc.max_v = __longlong_as_double(order_key(kmax_v));
     acc = block_combine(acc, sh_p);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
     if (HIST) {
