@@ -151,10 +151,17 @@ def cpu_baseline(model, scenario, n_sample: int):
     out = oracle.rollout(model, p, threads=cores)
     dt = time.perf_counter() - t0
     steps = int(out["n_steps"].astype(np.int64).sum())
+    # the same oracle on one thread, on 1/cores of the sample
+    n1 = max(1, n_sample // cores)
+    t1 = time.perf_counter()
+    oracle.rollout(model, {f: v[:n1] for f, v in p.items()}, threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {n_sample} of the N-sample workload (same seed), "
                       f"{steps} RK4 steps, {dt:.2f} s wall on {cores} threads",
-            "steps_per_s": steps / dt}
+            "steps_per_s": steps / dt,
+            "single_thread": {"value": n1 / dt1, "unit": UNIT,
+                              "sample": f"first {n1} samples, {dt1:.2f} s on 1 thread"}}
 
 
 def serve_run(aeb, m, seconds: float, rate: float):
