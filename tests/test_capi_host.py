@@ -208,3 +208,19 @@ def test_importance_sampler_matches_oracle(aeb, oracle_mod):
     with pytest.raises(aeb.AebError) as e:
         aeb.aeb_sample_params_is(m, p, ai.replace(q, tau=ai.uniform(0.1, 0.2)), 0, 10)
     assert e.value.code == aeb.EINVAL
+
+
+def test_readme_c_example_compiles_and_links(aeb, tmp_path):
+    """The C example in the README builds against include/aeb.h and links
+    against the library (it is not run: that needs a GPU)."""
+    text = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
+    assert len(blocks) == 1
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    exe = tmp_path / "example"
+    lib_dir = os.path.dirname(aeb._build.LIB)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), str(src), "-L", lib_dir, "-laeb", "-lm",
+                    f"-Wl,-rpath,{lib_dir}"], check=True)
+    assert exe.exists()
