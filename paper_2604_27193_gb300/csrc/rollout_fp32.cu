@@ -50,7 +50,8 @@
 //
 // Steps run in windows of up to K = 16 with no test in between.  A lane's
 // window ends before its next event (brake onset, the last step before the
-// horizon, a step that crosses a breakpoint of r(D)); lanes of a warp with
+// horizon, a step that crosses a breakpoint of r(D), and before a TTC trigger
+// the next step at which the trigger could fire); lanes of a warp with
 // shorter windows run the same window code masked, so a lane close to an event
 // does not hold up the others.  Brake onset is a change of state between two
 // steps (new command, new piece); only the breakpoint-crossing step and the
