@@ -90,6 +90,13 @@ FP64_CASES = {
                                               trigger=ai.TRIGGER_TTC, ttc_thr=3.0, perc_sigma=1.5,
                                               perc_drop=0.4, perc_latency=0.0123, perc_seed=12),
                                    ai.lead_braking_scenario(seed=22), 3_000),
+    # feature combinations at coarse steps
+    "ttc_perception_10ms": (ai.replace(ai.ttc_model(thr=2.0, dt=0.01), perc_sigma=0.8,
+                                       perc_drop=0.2, perc_latency=0.05, perc_seed=31),
+                            ai.single_scenario(seed=33), 3_000),
+    "moving_lead_ttc_5ms": (ai.replace(ai.lead_braking_model(dt=5e-3, lead_decel=4.0),
+                                       trigger=ai.TRIGGER_TTC, ttc_thr=3.0),
+                            ai.lead_braking_scenario(seed=34), 3_000),
 }
 
 
@@ -213,6 +220,13 @@ FP32_CASES = {
                     ai.single_scenario(seed=25), 10_000),
     # per-step actuator decay dt/tau up to 0.2
     "coarse_dt_20ms": (ai.single_model(dt=0.02), ai.single_scenario(seed=26), 10_000),
+    # feature combinations at coarse steps
+    "ttc_perception_10ms": (ai.replace(ai.ttc_model(thr=2.0, dt=0.01), perc_sigma=0.8,
+                                       perc_drop=0.2, perc_latency=0.05, perc_seed=32),
+                            ai.single_scenario(seed=35), 10_000),
+    "moving_lead_ttc_5ms": (ai.replace(ai.lead_braking_model(dt=5e-3, lead_decel=4.0),
+                                       trigger=ai.TRIGGER_TTC, ttc_thr=3.0),
+                            ai.lead_braking_scenario(seed=36), 10_000),
 }
 
 
