@@ -141,9 +141,44 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(model, scenario, n_sample: int):
+def cpu_baseline_configs(cores: int):
+    """The oracle on bounded samples of the batched-grid and TTC-sweep workloads
+    (all host cores): every 64th grid scenario with its first 500 samples, and 8
+    thresholds x 8 sweep scenarios x 500 samples."""
+    import oracle
+    res = {}
+    m = ai.single_model()
+    grid = ai.grid_scenarios(seed=2)[::64]
+    parts = [oracle.sample(m, sc, 0, min(n, 500)) for sc, n in grid]
+    p = {f: np.concatenate([q[f] for q in parts]) for f in ai.FIELDS}
+    n = len(p["v0"])
+    t0 = time.perf_counter()
+    oracle.rollout(m, p, threads=cores)
+    dt = time.perf_counter() - t0
+    res["batched_grid"] = {"value": n / dt, "unit": UNIT,
+                           "sample": f"{len(grid)} grid scenarios x <= 500 samples ({n} rollouts), "
+                                     f"{dt:.2f} s on {cores} threads"}
+    mt = ai.ttc_model()
+    scen = ai.ttc_scenarios(64, seed=4)[::8]
+    thr = ai.ttc_thresholds(256)[::32]
+    ps = [oracle.sample(mt, sc, 0, 500) for sc in scen]
+    q = {f: np.concatenate([x[f] for x in ps]) for f in ai.FIELDS}
+    t0 = time.perf_counter()
+    total = 0
+    for th in thr:
+        oracle.rollout(ai.replace(mt, ttc_thr=float(th)), q, threads=cores)
+        total += len(q["v0"])
+    dt = time.perf_counter() - t0
+    res["ttc_sweep"] = {"value": total / dt, "unit": UNIT,
+                        "sample": f"{len(thr)} thresholds x {len(scen)} scenarios x 500 samples "
+                                  f"({total} rollouts), {dt:.2f} s on {cores} threads"}
+    return res
+
+
+def cpu_baseline(model, scenario, n_sample: int, configs: bool = False):
     """The oracle as it stands, on all host cores, on the first n_sample samples
-    of the workload (the same sampler stream); extrapolated per rollout."""
+    of the workload (the same sampler stream); extrapolated per rollout.  With
+    ``configs``, also on samples of the batched-grid and TTC-sweep workloads."""
     import oracle
     cores = os.cpu_count() or 1
     p = oracle.sample(model, scenario, 0, n_sample)
@@ -156,12 +191,15 @@ def cpu_baseline(model, scenario, n_sample: int):
     t1 = time.perf_counter()
     oracle.rollout(model, {f: v[:n1] for f, v in p.items()}, threads=1)
     dt1 = time.perf_counter() - t1
-    return {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    line = {"value": n_sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {n_sample} of the N-sample workload (same seed), "
                       f"{steps} RK4 steps, {dt:.2f} s wall on {cores} threads",
             "steps_per_s": steps / dt,
             "single_thread": {"value": n1 / dt1, "unit": UNIT,
                               "sample": f"first {n1} samples, {dt1:.2f} s on 1 thread"}}
+    if configs:
+        line["configs"] = cpu_baseline_configs(cores)
+    return line
 
 
 def serve_run(aeb, m, seconds: float, rate: float):
@@ -697,7 +735,7 @@ def main():
                   "n_horizon": int(st.n_horizon), "p_contact": st.n_contact / st.n},
     }
     if single and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m, sc, args.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline(m, sc, args.cpu_sample, configs=not args.no_extras)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
