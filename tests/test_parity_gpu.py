@@ -376,3 +376,38 @@ def test_full_size_sampled(aeb, oracle_mod):
     exp = with_gap(oracle_mod.rollout(m, sub, threads=8), sub, m)
     g = with_gap({k: v[idx] for k, v in got.items()}, sub, m)
     fp32_report(m, g, exp)
+
+
+def test_full_size_fp64_sampled(aeb, oracle_mod):
+    """The binary64 kernel on the full N = 1e7 single-scenario launch (the
+    bench's comparison arm): every output of 2,000 sampled samples, and the
+    first and last ones, bit-identical to the oracle."""
+    m = ai.single_model()
+    n = 10_000_000
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=0), 0, n)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n)
+    aeb.aeb_rollout(m, P, n, aeb.FP64_PLAIN, O)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 2000), [0, 1, n - 2, n - 1]]))
+    got = {k: v.cpu().numpy()[idx] for k, v in O.items()}
+    exp = oracle_mod.rollout(m, {f: p[f][idx] for f in ai.FIELDS}, threads=8)
+    assert_bit_exact(got, exp)
+
+
+def test_full_size_fine_step_sampled(aeb, oracle_mod):
+    """The FP32-compensated kernel on N = 1e7 at dt = 0.1 ms (the largest cell of
+    the N x dt sweep, ~3.2e11 RK4 steps): 1,000 sampled samples against the
+    oracle within the FP32 bounds."""
+    m = ai.single_model(dt=1e-4)
+    n = 10_000_000
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=0), 0, n)
+    P = {f: torch.from_numpy(p[f]).cuda() for f in ai.FIELDS}
+    O = aeb.alloc_outputs(n)
+    aeb.aeb_rollout(m, P, n, aeb.FP32_COMP, O)
+    rng = np.random.default_rng(2)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 1000), [0, n - 1]]))
+    sub = {f: p[f][idx] for f in ai.FIELDS}
+    exp = with_gap(oracle_mod.rollout(m, sub, threads=8), sub, m)
+    g = with_gap({k: v.cpu().numpy()[idx] for k, v in O.items()}, sub, m)
+    print("fine step", fp32_report(m, g, exp))
