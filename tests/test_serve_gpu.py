@@ -175,3 +175,30 @@ def test_perception_request_alone_equals_in_mix(aeb):
             assert srv.poll(tk)[0] == aeb.OK
     finally:
         srv.close()
+
+
+def test_largest_request_alone_equals_in_mix(aeb):
+    """The bench's serving configuration with a request of 1e6 samples (the
+    serving maximum): its statistics are the same bits alone and amid a
+    stream of requests of 1e3 to 1e6 samples, and it completes well inside the
+    530 ms budget alone."""
+    srv = aeb.Server(ai.single_model(), aeb.FP32_COMP, arena_rows=1 << 23,
+                     chunk_samples=1 << 18, wave_samples=1 << 21, max_waves_in_flight=2,
+                     sampler_threads=0, max_request_samples=1_000_000)
+    try:
+        sc = ai.scenario_from_means(30.0, 0.5, 0.9, 70.0, seed=6, scenario_id=91)
+        t = srv.submit(sc, 1_000_000)
+        code, alone, lat = srv.poll(t)
+        assert code == aeb.OK and alone.n == 1_000_000
+        assert lat.total_ms < 530.0, lat.total_ms
+        reqs = ai.request_stream(rate=400.0, duration=0.05, seed=12)
+        tickets = [srv.submit(s, n) for _, s, n in reqs[:8]]
+        tA = srv.submit(sc, 1_000_000)
+        tickets += [srv.submit(s, n) for _, s, n in reqs[8:16]]
+        code, mixed, _ = srv.poll(tA)
+        assert code == aeb.OK
+        assert same(alone, mixed), "the 1e6-sample request changed with its company"
+        for tk in tickets:
+            assert srv.poll(tk)[0] == aeb.OK
+    finally:
+        srv.close()
