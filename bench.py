@@ -496,8 +496,8 @@ def rare_event_run(aeb, torch):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        est, se, ci = aeb.is_estimate(aeb.wstats_from_buffer(S))
-        res[name] = {"samples": n, "ms": ms, "p": est, "se": se, "ci95": list(ci)}
+        r = aeb.aeb_is_estimate(aeb.wstats_from_buffer(S))
+        res[name] = {"samples": n, "ms": ms, "p": r.p, "se": r.se, "ci95": [r.ci_lo, r.ci_hi]}
         del P, W, O
     pl, im = res["plain"], res["importance"]
     p_ref = pl["p"]
@@ -510,17 +510,73 @@ def rare_event_run(aeb, torch):
             "precision": "fp32-compensated"}
 
 
+def fp32_error_table(aeb, torch, O32, O64, st32, st64):
+    """FP32-compensated outputs against the binary64 ones on the same samples
+    (the bounds of the parity tests, measured over the whole launch): per-sample
+    errors of every output on the device (reading only) and the moments of the
+    two reductions."""
+    s32, s64 = O32["status"], O64["status"]
+    same = s32 == s64
+    stop = same & (s64 == 0)
+    cont = same & (s64 == 1)
+    x64 = O64["x_ref"][stop]
+    rel = ((O32["x_ref"][stop] - x64).abs() / x64.abs().clamp_min(1e-3))
+    ns_eq = same & (O32["n_steps"] == O64["n_steps"])
+    xr64 = O64["x_raw"][ns_eq]
+    xr_rel = ((O32["x_raw"][ns_eq] - xr64).abs() / xr64.abs().clamp_min(1e-3))
+    dte = (O32["t_end"][stop] - O64["t_end"][stop]).abs()
+    dvi = (O32["v_imp"][cont] - O64["v_imp"][cont]).abs()
+    a, b = aeb.aeb_stats_summary(st32), aeb.aeb_stats_summary(st64)
+    f = lambda t: float(t.max()) if t.numel() else 0.0
+    return {
+        "samples": int(s64.numel()),
+        "flag_disagree": int((~same).sum()),
+        "onset_disagree": int((O32["n_onset"] != O64["n_onset"]).sum()),
+        "n_steps_disagree": int((same & (O32["n_steps"] != O64["n_steps"])).sum()),
+        "x_ref_rel_max": f(rel), "x_ref_rel_mean": float(rel.mean()) if rel.numel() else 0.0,
+        "x_raw_rel_max": f(xr_rel),
+        "stop_t_end_abs_max_s": f(dte), "v_imp_abs_max_mps": f(dvi),
+        "sum_d_rel": abs(st32.sum_d - st64.sum_d) / abs(st64.sum_d),
+        "mean_d_rel": abs(a.mean_d - b.mean_d) / abs(b.mean_d),
+        "std_d_rel": abs(a.std_d - b.std_d) / abs(b.std_d),
+        "mean_v_rel": abs(a.mean_v - b.mean_v) / abs(b.mean_v) if b.n_contact else None,
+        "p_contact_abs": abs(a.p_contact - b.p_contact),
+        "bounds": "x_ref, x_raw <= 1e-5 relative; flags only where |gap| < 1e-3 m; "
+                  "moments follow (parity tests)"}
+
+
+def pooled_stats(aeb, torch, dist, S, world, dev):
+    """The exchange step of a sharded run: every rank's fixed-size statistics,
+    all-gathered and merged in rank order with aeb_stats_merge (counts and
+    histograms exact; the same bits every run)."""
+    if dist:
+        parts = [torch.empty_like(S) for _ in range(world)]
+        dist.all_gather(parts, S)
+    else:
+        parts = [S]
+    acc = aeb.empty_stats(aeb.hist_spec())
+    for part in parts:
+        aeb.aeb_stats_merge(acc, aeb.stats_from_buffer(part))
+    sm = aeb.aeb_stats_summary(acc)
+    lo, hi = aeb.aeb_hist_quantile(acc, 0.99)
+    return {"ranks": world, "n": int(sm.n), "n_contact": int(sm.n_contact),
+            "n_stop": int(sm.n_stop), "p_contact": sm.p_contact,
+            "p_contact_ci95": [sm.p_contact_lo, sm.p_contact_hi],
+            "mean_d_m": sm.mean_d, "std_d_m": sm.std_d, "d_stop_q99_bin_m": [lo, hi],
+            "how": "all_gather of aeb_stats, aeb_stats_merge in rank order"}
+
+
 def model_of(args):
     if args.ttc_thr is not None:
         return ai.ttc_model(thr=args.ttc_thr, dt=args.dt)
     return ai.single_model(dt=args.dt)
 
 
-def config(args, world):
+def config(args, world, precision="fp32-compensated"):
     trig = "immediate trigger" if args.ttc_thr is None else f"TTC trigger at {args.ttc_thr:g} s"
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         f"10 s horizon, lead at d0, per-axle caps, {trig}",
-            "n_samples_per_gpu": args.n, "dt_s": args.dt, "precision": "fp32-compensated",
+            "n_samples_per_gpu": args.n, "dt_s": args.dt, "precision": precision,
             "l2": "inputs 800 MB per GPU > 129 MB L2, no flush",
             "parallelism": f"replicas x{world} (independent sample shards)"}
 
@@ -545,7 +601,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(args, world),
+            "data": "synthetic",
+            "config": config(args, world, precision="binary64 CPU oracle (plain definition)"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n_step} samples of the workload per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -626,24 +683,42 @@ def main():
     achieved = steps_per_launch * FLOPS_PER_STEP / (roll_ms / 1e3) / 1e12
 
     # ---- FP64 plain on the same samples ----------------------------------
+    pooled = pooled_stats(aeb, torch, dist, S, world, dev)
     fp64 = None
     if not args.no_fp64:
-        for _ in range(1):
-            step(aeb.FP64_PLAIN)
+        # the binary64 step writes every output, so that the FP32 error can be
+        # stated for each; one untimed FP32 launch gives the FP32 side
+        O64 = aeb.alloc_outputs(N, device=dev)
+        S64 = aeb.alloc_stats(dev)
+
+        def step64():
+            aeb.aeb_rollout(m, P, N, aeb.FP64_PLAIN, O64, stream)
+            aeb.aeb_reduce(O64, N, hist, S64, stream)
+
+        step64()
         barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         for _ in range(args.fp64_steps):
-            step(aeb.FP64_PLAIN)
+            step64()
         s1.record(stream)
         barrier()
         ms64 = max_over_ranks(s0.elapsed_time(s1)) / args.fp64_steps
+        O32 = aeb.alloc_outputs(N, device=dev)
+        S32 = aeb.alloc_stats(dev)
+        aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O32, stream)
+        aeb.aeb_reduce(O32, N, hist, S32, stream)
+        torch.cuda.synchronize()
+        err = fp32_error_table(aeb, torch, O32, O64, aeb.stats_from_buffer(S32),
+                               aeb.stats_from_buffer(S64))
+        del O32, O64, S32, S64
         fp64 = {"value": world * N / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                 "steps": args.fp64_steps, "warmup": 1, "dtype": "f64",
                 "achieved_tflops": steps_per_launch * FLOPS_PER_STEP / (ms64 / 1e3) / 1e12,
                 "peak_tflops_nominal": FP64_PEAK_TFLOPS,
                 "note": "no fused multiply-add on this path: its bound is the binary64 "
-                        "add/multiply rate (measured_pipe_peaks.fp64_add_tops)"}
+                        "add/multiply rate (measured_pipe_peaks.fp64_add_tops)",
+                "fp32_error": err}
 
     # ---- end to end through the public host-buffer call ------------------
     aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)  # sizes the buffers
@@ -657,6 +732,20 @@ def main():
     e2e = {"value": world * N * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * len(ai.FIELDS) * N, "d2h_bytes_per_step": aeb.STATS_BYTES,
            "api": "aeb_evaluate (pinned host params -> host stats)"}
+    # the same, from the seed: host sampling (all host threads) inside the step
+    barrier()
+    t0 = time.perf_counter()
+    ts = 0.0
+    for _ in range(e2e_steps):
+        t1 = time.perf_counter()
+        aeb.aeb_sample_params(m, sc, 0, N, host)
+        ts += time.perf_counter() - t1
+        aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)
+    barrier()
+    e2ws_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_sampling = {"value": world * N * e2e_steps / e2ws_s, "unit": UNIT,
+                    "host_sampling_s_per_step": ts / e2e_steps, "host_threads": os.cpu_count(),
+                    "api": "aeb_sample_params (pinned host columns) + aeb_evaluate"}
 
     peaks = aeb.aeb_pipe_peaks(stream)
     if rank != 0:  # the remaining lines are single-GPU measurements, taken by rank 0
@@ -733,9 +822,26 @@ def main():
         "host_sampling_s": t_sample,
         "stats": {"n_stop": int(st.n_stop), "n_contact": int(st.n_contact),
                   "n_horizon": int(st.n_horizon), "p_contact": st.n_contact / st.n},
+        "pooled": pooled,
+        "e2e_with_sampling": e2e_sampling,
     }
     if single and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, sc, args.cpu_sample, configs=not args.no_extras)
+    # the whole headline metric in one compact block, last in the line
+    head = {"fp32_comp_rollouts_per_s": value,
+            "fp64_plain_rollouts_per_s": fp64["value"] if fp64 else None,
+            "fp32_over_fp64": (value / fp64["value"]) if fp64 else None,
+            "fp32_roofline_frac": achieved / FP32_PEAK_TFLOPS,
+            "e2e_rollouts_per_s": e2e["value"],
+            "e2e_with_sampling_rollouts_per_s": e2e_sampling["value"]}
+    if fp64:
+        e = fp64["fp32_error"]
+        head["fp32_error"] = {k: e[k] for k in ("x_ref_rel_max", "x_raw_rel_max", "flag_disagree",
+                                                "mean_d_rel", "std_d_rel", "mean_v_rel")}
+    if serving:
+        head["serving"] = {k: serving[k] for k in ("requests", "p50_ms", "p99_ms", "p999_ms",
+                                                   "max_ms", "budget_ms", "p99_within_budget")}
+    line["headline"] = head
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define AEB_ABI_VERSION 4
+#define AEB_ABI_VERSION 5
 #define AEB_NFIELDS 10   /* columns of a parameter set, see aeb_params       */
 #define AEB_NBINS 4096   /* bins of each fixed histogram in aeb_stats         */
 
@@ -65,6 +65,7 @@ enum { AEB_CAP_LUMPED = 0, AEB_CAP_PER_AXLE = 1 };
 enum { AEB_TRIGGER_IMMEDIATE = 0, AEB_TRIGGER_TTC = 1 };
 enum { AEB_STOP = 0, AEB_CONTACT = 1, AEB_HORIZON = 2, AEB_INVALID = 255 };
 enum { AEB_DIST_CONST = 0, AEB_DIST_UNIFORM = 1, AEB_DIST_NORMAL = 2 };
+enum { AEB_HIST_D = 0, AEB_HIST_V = 1 };  /* stopping-distance / impact-speed histogram */
 
 /* ---- model constants (Sec. III, Sec. IV-B) ------------------------------- */
 typedef struct aeb_model {
@@ -245,6 +246,40 @@ typedef struct aeb_wstats {
     double sum_w, sumsq_w;         /* sum of w and of w^2 over valid samples       */
     double sum_we, sumsq_we;       /* sum of w 1[E] and of (w 1[E])^2              */
 } aeb_wstats;
+
+/* Summary of a reduction (Sec. VI-B, Table I: mean, standard deviation and
+ * range of the stopping distance; the collision probability).  Means and
+ * unbiased standard deviations come from the sums of the statistics:
+ * m = s / k, sd = sqrt((ss - (k m) m) / (k - 1)) (negative variance from
+ * cancellation clamped to 0).  Fields of an empty set are NaN; sd needs two
+ * values. */
+typedef struct aeb_summary {
+    uint64_t n, n_valid;                   /* samples; n - n_invalid          */
+    uint64_t n_stop, n_contact, n_horizon, n_invalid;
+    uint64_t steps;                        /* RK4 steps executed in total     */
+    double mean_steps;                     /* steps / n                       */
+    double mean_d, std_d, min_d, max_d;    /* x_ref over stopped samples [m]  */
+    double mean_v, std_v, min_v, max_v;    /* v_imp over contact samples [m/s] */
+    double p_contact;                      /* n_contact / n_valid             */
+    double p_contact_lo, p_contact_hi;     /* 95 % Wilson score interval      */
+} aeb_summary;
+
+/* A probability estimated from k events in n trials, with its 95 % Wilson
+ * score interval. */
+typedef struct aeb_prob {
+    uint64_t k, n;
+    double p;              /* k / n (NaN if n == 0)                          */
+    double ci_lo, ci_hi;
+} aeb_prob;
+
+/* Importance-sampling estimate of an event probability under the nominal
+ * scenario (aeb_is_estimate). */
+typedef struct aeb_is_result {
+    uint64_t n, n_event;   /* samples, valid samples in the event             */
+    double p;              /* sum_we / n                                      */
+    double se;             /* standard error (NaN below two samples)          */
+    double ci_lo, ci_hi;   /* p -+ 1.959963984540054 se                       */
+} aeb_is_result;
 
 /* Collision probability at one TTC threshold, pooled over the scenarios
  * (Sec. VI-C, Eq. 19 with the TTC = H0 / v criterion). */
@@ -514,6 +549,60 @@ aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *scenarios, 
  */
 aeb_status aeb_stats_merge(aeb_stats *acc, const aeb_stats *part);
 aeb_status aeb_job_stats_merge(aeb_job_stats *acc, const aeb_job_stats *part);
+
+/*
+ * aeb_stats_summary / aeb_job_stats_summary -- the summary of a reduction
+ * (host memory; see aeb_summary): counts, the mean, standard deviation and
+ * range of the stopping distance over stopped samples and of the impact
+ * speed over contact samples (Sec. VI-B, Table I), and the collision
+ * probability n_contact / n_valid with its 95 % Wilson interval.
+ * Host only, allocates nothing.  AEB_EINVAL: NULL argument, or counts that do
+ * not add up to n.
+ */
+aeb_status aeb_stats_summary(const aeb_stats *stats, aeb_summary *out);
+aeb_status aeb_job_stats_summary(const aeb_job_stats *stats, aeb_summary *out);
+
+/*
+ * aeb_hist_quantile -- the bin of a fixed histogram of `stats` (host memory)
+ * that holds its q-quantile, i.e. the order statistic x_(k), k = ceil(q N)
+ * clamped to [1, N], of the N samples the histogram counts (which =
+ * AEB_HIST_D: x_ref of the stopped samples; AEB_HIST_V: v_imp of the contact
+ * samples).  The safe headway at risk level p is the (1 - p) quantile of the
+ * stopping distance (Sec. VI-C: 5, 1 and 0.1 % risk); *hi is then the
+ * conservative value.  On return x_(k) lies in [*lo, *hi), a bin of width w;
+ * the first bin starts at -inf and the last ends at +inf, because values
+ * beyond the histogram's range are counted in its end bins.
+ * Host only.  AEB_EINVAL: NULL argument, q outside [0, 1], unknown `which`,
+ * an empty histogram, or a histogram whose bins do not add up to its count.
+ */
+aeb_status aeb_hist_quantile(const aeb_stats *stats, int32_t which, double q, double *lo,
+                             double *hi);
+
+/*
+ * aeb_hist_exceedance -- P(X >= x) read off a fixed histogram of `stats` at
+ * an inner bin edge x = lo + j w, 1 <= j <= AEB_NBINS - 1: the samples of the
+ * histogram in bins j and above, over the valid samples (n - n_invalid), with
+ * the 95 % Wilson interval.  With X = the stopping distance and x = H0 this is
+ * Eq. 19's P(D_stop > H0) (Sec. VI-C; no sample lies exactly on an edge unless
+ * the inputs put it there): exact, because every bin at or above j holds only
+ * values >= x.  With a lead vehicle, contact and horizon samples count as
+ * trials but not as events (their stopping distance is not observed); their
+ * share is p_contact of aeb_stats_summary.
+ * Host only.  AEB_EINVAL: NULL argument, unknown `which`, x not such an edge,
+ * a histogram whose bins do not add up to its count.
+ */
+aeb_status aeb_hist_exceedance(const aeb_stats *stats, int32_t which, double x, aeb_prob *out);
+
+/*
+ * aeb_is_estimate -- the importance-sampling estimate of an event's
+ * probability under the nominal scenario from the weighted sums of
+ * aeb_reduce_weighted (host memory; rare-event estimation, Sec. VIII): p =
+ * sum_we / n, its standard error sqrt(var / n) with the unbiased sample
+ * variance var = (sumsq_we - (n p) p) / (n - 1), and the 95 % normal interval
+ * p -+ 1.959963984540054 se.  Host only.  AEB_EINVAL: NULL argument, counts
+ * that are inconsistent (n_event > n_valid > n).
+ */
+aeb_status aeb_is_estimate(const aeb_wstats *ws, aeb_is_result *out);
 
 /* Wilson score interval of k successes in n trials at normal quantile z
  * (z = 1.959963984540054 for 95 %).  n == 0 gives [0, 1]. */

@@ -59,6 +59,12 @@ class _Stats(C.Structure):
                                   "sum_v", "sumsq_v", "min_v", "max_v")]
 
 
+class _Probe(C.Structure):
+    _fields_ = [("force", C.c_int64), ("lo", C.c_int64), ("hi", C.c_int64),
+                ("x", C.POINTER(C.c_double)), ("gap_meas", C.POINTER(C.c_double)),
+                ("thr_closing", C.POINTER(C.c_double)), ("reading", C.POINTER(C.c_int8))]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -104,6 +110,11 @@ def lib():
             L.om_sample_is.argtypes = [P(_Model), P(_Scenario), P(_Scenario), C.c_uint64,
                                        C.c_uint64, P(P(C.c_double)), P(C.c_double)]
             L.om_sample_is.restype = C.c_int
+            L.om_rollout_probe.argtypes = [P(_Model), P(P(C.c_double)), C.c_uint64, C.c_uint64,
+                                           P(_Probe), P(C.c_uint8), P(C.c_double),
+                                           P(C.c_double), P(C.c_double), P(C.c_double),
+                                           P(C.c_int32), P(C.c_int32)]
+            L.om_rollout_probe.restype = C.c_int
             _lib = L
     return _lib
 
@@ -229,6 +240,36 @@ def rollout(model, params: dict, threads: int = 1, row0: int = 0) -> dict:
     return out
 
 
+def rollout_probe(model, params: dict, i: int, row: int | None = None, force: int = -2,
+                  lo: int = 0, hi: int = 0):
+    """Sample i of ``params`` (perception row ``row``, default i) with the TTC
+    trigger's test hook: ``force`` >= 0 fires the trigger at that step, -1
+    never, -2 leaves the margin test in charge.  Returns (outputs, record):
+    outputs as ``rollout`` gives them for this one sample, record a dict of
+    arrays over steps [lo, hi): position x_n, measured gap, ttc_thr times the
+    closing speed (NaN where the trigger was not tested) and whether the
+    reading was present (-1 where not tested).  Test infrastructure for the
+    binary32 kernel's trigger ties only."""
+    k = max(0, hi - lo)
+    rec = {"x": np.full(k, np.nan), "gap_meas": np.full(k, np.nan),
+           "thr_closing": np.full(k, np.nan), "reading": np.full(k, -1, dtype=np.int8)}
+    pr = _Probe(force, lo, hi, _dptr(rec["x"]), _dptr(rec["gap_meas"]), _dptr(rec["thr_closing"]),
+                rec["reading"].ctypes.data_as(C.POINTER(C.c_int8)))
+    arr, keep = _cols_array(params)
+    st, on, ns = C.c_uint8(), C.c_int32(), C.c_int32()
+    xr, xf, vi, te = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    m = _model(model)
+    ok = lib().om_rollout_probe(C.byref(m), arr, i, i if row is None else row, C.byref(pr),
+                                C.byref(st), C.byref(xr), C.byref(xf), C.byref(vi), C.byref(te),
+                                C.byref(ns), C.byref(on))
+    del keep
+    if not ok:
+        raise ValueError("invalid sample")
+    out = {"status": st.value, "x_raw": xr.value, "x_ref": xf.value, "v_imp": vi.value,
+           "t_end": te.value, "n_steps": ns.value, "n_onset": on.value}
+    return out, rec
+
+
 def axle_cap(model, mu: float, gc: float, D: float) -> float:
     """Realised deceleration for demanded deceleration D (Eq. 5 / per-axle reading)."""
     m = _model(model)
@@ -285,6 +326,24 @@ def reduce(out: dict, lo_d: float = 0.0, w_d: float = 0.125, lo_v: float = 0.0,
                     hv.ctypes.data_as(P(C.c_uint64)), lo_v, w_v, nbins)
     vals = {name: getattr(st, name) for name, _ in _Stats._fields_}
     return Stats(**vals, hist_d=hd, hist_v=hv)
+
+
+def moments(values):
+    """Mean and unbiased standard deviation of a set of values (Sec. VI-B,
+    Table I: mean and standard deviation of the stopping distance), by their
+    plain definitions: m = sum(x) / k, sd = sqrt(sum((x - m)^2) / (k - 1)),
+    both sums exactly rounded (math.fsum).  (nan, nan) for an empty set; sd is
+    nan below two values."""
+    import math
+    x = np.asarray(values, dtype=np.float64)
+    k = len(x)
+    if k == 0:
+        return float("nan"), float("nan")
+    m = math.fsum(x) / k
+    if k < 2:
+        return m, float("nan")
+    r = x - m
+    return m, math.sqrt(math.fsum(r * r) / (k - 1))
 
 
 def quantile(values: np.ndarray, q: float) -> float:

@@ -28,6 +28,9 @@
  *   om_philox4x64_10   pinned: numpy's Philox4x64-10 bit generator.
  *   om_sample          pinned: Kolmogorov-Smirnov / moment tests against scipy
  *                      distributions, clamping and counter-layout invariants.
+ *   om_rollout_probe   pinned: equal to om_rollout without an override; the
+ *                      recorded margins against the closed form of a car at
+ *                      constant speed and against the trigger step it reports.
  *   om_rollout         pinned: closed forms (constant deceleration, constant
  *                      deceleration + quadratic drag, pure actuator lag, grade,
  *                      contact kinematics, TTC trigger step, moving-lead contact
@@ -463,6 +466,26 @@ int om_perception(const om_model *m, uint64_t row, int64_t k, double *noise)
 }
 
 /*
+ * Test hook of the TTC trigger, used only to check the binary32 kernel's
+ * trigger decisions (which may differ from these where the trigger margin is
+ * within rounding of zero).  With force >= 0 the trigger fires at step
+ * `force` exactly, with force == -1 never, in place of the margin test; with
+ * force == -2 nothing is overridden.  For each step n in [lo, hi) at which the
+ * trigger is still tested, the position x_n, the measured gap (with the range
+ * noise and the reading's noise) and ttc_thr times the closing speed are
+ * recorded, and whether the reading is present (steps not tested are left as
+ * the caller set them).
+ */
+typedef struct {
+    int64_t force;
+    int64_t lo, hi;
+    double *x;
+    double *gap_meas;
+    double *thr_closing;
+    int8_t *reading;
+} om_probe;
+
+/*
  * One rollout (Sec. IV-D): classic RK4 on Eq. 7-9 with the command held over
  * the step, until contact, stop (v <= 0, Sec. V-D) or the horizon.
  *
@@ -495,7 +518,7 @@ int om_perception(const om_model *m, uint64_t row, int64_t k, double *noise)
  */
 static void rollout_one(const om_model *m, const om_consts *c, uint64_t row, uint8_t *status,
                         double *x_raw, double *x_ref, double *v_imp, double *t_end,
-                        int32_t *n_steps, int32_t *n_onset)
+                        int32_t *n_steps, int32_t *n_onset, const om_probe *pr)
 {
     const double dt = m->dt;
     const double h2 = 0.5 * dt;
@@ -538,7 +561,18 @@ static void rollout_one(const om_model *m, const om_consts *c, uint64_t row, uin
                 reading = perception(m, row, n + lat, &pn);
                 gap_meas = gap_meas + pn;
             }
-            if (reading && gap_meas <= m->ttc_thr * closing) {
+            int fire = reading && gap_meas <= m->ttc_thr * closing;
+            if (pr) {
+                if (n >= pr->lo && n < pr->hi) {
+                    const int64_t j = n - pr->lo;
+                    pr->x[j] = x;
+                    pr->gap_meas[j] = gap_meas;
+                    pr->thr_closing[j] = m->ttc_thr * closing;
+                    pr->reading[j] = (int8_t)reading;
+                }
+                if (pr->force != -2) fire = (n == pr->force);
+            }
+            if (fire) {
                 triggered = 1; n_b = (n + lat) + c->n_delay;
                 *n_onset = (n_b > 2147483647) ? 2147483647 : (int32_t)n_b;
             }
@@ -612,9 +646,22 @@ int om_rollout(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t
             continue;
         }
         rollout_one(m, &c, row0 + i, &status[i], &x_raw[i], &x_ref[i], &v_imp[i], &t_end[i],
-                    &n_steps[i], &n_onset[i]);
+                    &n_steps[i], &n_onset[i], NULL);
     }
     return 0;
+}
+
+/* One sample (column index i, perception row `row`) with the TTC test hook
+ * `pr`; returns 0 (outputs untouched) if the sample is invalid. */
+int om_rollout_probe(const om_model *m, const double *const cols[OM_NFIELDS], uint64_t i,
+                     uint64_t row, const om_probe *pr, uint8_t *status, double *x_raw,
+                     double *x_ref, double *v_imp, double *t_end, int32_t *n_steps,
+                     int32_t *n_onset)
+{
+    om_consts c;
+    if (!make_consts(m, cols, i, &c)) return 0;
+    rollout_one(m, &c, row, status, x_raw, x_ref, v_imp, t_end, n_steps, n_onset, pr);
+    return 1;
 }
 
 /* ------------------------------------------------------------------------- */

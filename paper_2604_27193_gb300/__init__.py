@@ -13,7 +13,6 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -25,11 +24,12 @@ OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
 OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
               "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
               "n_onset": np.int32}
-ABI_VERSION = 4  # AEB_ABI_VERSION of include/aeb.h
+ABI_VERSION = 5  # AEB_ABI_VERSION of include/aeb.h
 NBINS = 4096
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)
 FP64_PLAIN, FP32_COMP = 0, 1
+HIST_D, HIST_V = 0, 1
 STOP, CONTACT, HORIZON, INVALID = 0, 1, 2, 255
 
 
@@ -124,6 +124,24 @@ class WStats(C.Structure):
         (n, C.c_double) for n in ("sum_w", "sumsq_w", "sum_we", "sumsq_we")]
 
 
+class Summary(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("n", "n_valid", "n_stop", "n_contact", "n_horizon",
+                                          "n_invalid", "steps")] + \
+        [(n, C.c_double) for n in ("mean_steps", "mean_d", "std_d", "min_d", "max_d", "mean_v",
+                                   "std_v", "min_v", "max_v", "p_contact", "p_contact_lo",
+                                   "p_contact_hi")]
+
+
+class Prob(C.Structure):
+    _fields_ = [("k", C.c_uint64), ("n", C.c_uint64), ("p", C.c_double), ("ci_lo", C.c_double),
+                ("ci_hi", C.c_double)]
+
+
+class IsResult(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("n_event", C.c_uint64)] + [
+        (n, C.c_double) for n in ("p", "se", "ci_lo", "ci_hi")]
+
+
 STATS_BYTES = C.sizeof(Stats)
 WSTATS_BYTES = C.sizeof(WStats)
 JOB_STATS_BYTES = C.sizeof(JobStats)
@@ -179,12 +197,19 @@ def lib():
             L.aeb_serve_counters_get.argtypes = [C.c_void_p, P(ServeCounters)]
             L.aeb_serve_destroy.argtypes = [C.c_void_p]
             L.aeb_serve_destroy.restype = None
+            L.aeb_stats_summary.argtypes = [P(Stats), P(Summary)]
+            L.aeb_job_stats_summary.argtypes = [P(JobStats), P(Summary)]
+            L.aeb_hist_quantile.argtypes = [P(Stats), C.c_int32, C.c_double, P(C.c_double),
+                                            P(C.c_double)]
+            L.aeb_hist_exceedance.argtypes = [P(Stats), C.c_int32, C.c_double, P(Prob)]
+            L.aeb_is_estimate.argtypes = [P(WStats), P(IsResult)]
             for fn in ("aeb_sample_params", "aeb_rollout", "aeb_reduce", "aeb_evaluate",
                        "aeb_batch_create", "aeb_batch_run", "aeb_rollout_batched",
                        "aeb_get_launch_config", "aeb_set_launch_config", "aeb_autotune",
                        "aeb_serve_create", "aeb_serve_submit", "aeb_serve_poll",
                        "aeb_serve_cancel", "aeb_serve_counters_get", "aeb_sample_params_is",
-                       "aeb_reduce_weighted"):
+                       "aeb_reduce_weighted", "aeb_stats_summary", "aeb_job_stats_summary",
+                       "aeb_hist_quantile", "aeb_hist_exceedance", "aeb_is_estimate"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != ABI_VERSION:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -303,14 +328,12 @@ def wstats_from_buffer(buf) -> WStats:
     return WStats.from_buffer_copy(raw)
 
 
-def is_estimate(ws: WStats):
-    """Unbiased importance-sampling estimate of the event probability under the
-    nominal law, its standard error and the 95 % normal interval."""
-    n = ws.n
-    p = ws.sum_we / n
-    var = (ws.sumsq_we - n * p * p) / (n - 1) if n > 1 else float("nan")
-    se = float(np.sqrt(max(var, 0.0) / n))
-    return p, se, (p - 1.959963984540054 * se, p + 1.959963984540054 * se)
+def aeb_is_estimate(ws: WStats) -> IsResult:
+    """Importance-sampling estimate of the event probability under the nominal
+    law, its standard error and the 95 % interval (computed by the library)."""
+    r = IsResult()
+    _check(lib().aeb_is_estimate(C.byref(ws), C.byref(r)))
+    return r
 
 
 def aeb_rollout(m, params: dict, n: int, precision: int, out: dict, stream=None):
@@ -561,41 +584,30 @@ def stats_from_buffer(buf) -> Stats:
     return Stats.from_buffer_copy(raw)
 
 
-@dataclass
-class Summary:
-    n: int
-    n_stop: int
-    n_contact: int
-    n_horizon: int
-    n_invalid: int
-    steps: int
-    mean_d: float
-    std_d: float
-    min_d: float
-    max_d: float
-    mean_v: float
-    p_contact: float
+def aeb_stats_summary(st: Stats) -> Summary:
+    """Counts, mean / standard deviation / range of D_stop and v_imp and the
+    collision probability with its Wilson interval (library call)."""
+    r = Summary()
+    _check(lib().aeb_stats_summary(C.byref(st), C.byref(r)))
+    return r
 
 
-def summarize(st: Stats) -> Summary:
-    def mean_std(s, ss, k):
-        if k == 0:
-            return float("nan"), float("nan")
-        m = s / k
-        var = (ss - k * m * m) / (k - 1) if k > 1 else 0.0
-        return m, float(np.sqrt(max(var, 0.0)))
-    md, sd = mean_std(st.sum_d, st.sumsq_d, st.n_stop)
-    mv, _ = mean_std(st.sum_v, st.sumsq_v, st.n_contact)
-    return Summary(st.n, st.n_stop, st.n_contact, st.n_horizon, st.n_invalid, st.steps, md,
-                   sd, st.min_d, st.max_d, mv, st.n_contact / st.n if st.n else float("nan"))
+def aeb_job_stats_summary(st: JobStats) -> Summary:
+    """aeb_stats_summary of a per-job reduction (library call)."""
+    r = Summary()
+    _check(lib().aeb_job_stats_summary(C.byref(st), C.byref(r)))
+    return r
 
 
-def hist_quantile(st: Stats, q: float) -> float:
-    """Upper edge of the stopping-distance bin that holds the q-quantile
-    (inverted-CDF definition), i.e. within one bin width above the exact
-    order statistic."""
-    h = np.frombuffer(bytes(st.hist_d), dtype=np.uint64).astype(np.int64)
-    k = int(np.ceil(q * st.n_stop))
-    k = min(max(k, 1), int(st.n_stop))
-    j = int(np.searchsorted(np.cumsum(h), k))
-    return st.lo_d + (j + 1) * st.w_d
+def aeb_hist_quantile(st: Stats, q: float, which: int = HIST_D):
+    """(lo, hi): the histogram bin that holds the q-quantile (library call)."""
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().aeb_hist_quantile(C.byref(st), which, q, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def aeb_hist_exceedance(st: Stats, x: float, which: int = HIST_D) -> Prob:
+    """P(X >= x) at an inner bin edge x, with its Wilson interval (library call)."""
+    r = Prob()
+    _check(lib().aeb_hist_exceedance(C.byref(st), which, x, C.byref(r)))
+    return r

@@ -31,7 +31,7 @@ CU_SOURCES = {
     "reduce_weighted.cu": [],
     "peaks.cu": ["-fmad=true"],
 }
-CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp", "sweep.cpp"]
+CPP_SOURCES = ["capi.cpp", "sampler.cpp", "batch.cpp", "serve.cpp", "sweep.cpp", "stats.cpp"]
 HEADERS = ["aeb_internal.h", "rollout_common.cuh", "host_util.h"]
 
 

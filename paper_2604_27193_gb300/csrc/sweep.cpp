@@ -1,76 +1,12 @@
 // sweep.cpp -- the TTC-threshold sweep: collision probability with a 95 %
-// Wilson interval at each threshold, pooled over scenarios, from batched
-// launches that share one resident parameter block.
+// Wilson interval at each threshold (aeb_wilson, stats.cpp), pooled over
+// scenarios, from batched launches that share one resident parameter block.
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "aeb_internal.h"
 #include "host_util.h"
-
-extern "C" aeb_status aeb_wilson(uint64_t k, uint64_t n, double z, double *lo, double *hi)
-{
-    aeb::clear_error();
-    if (!lo || !hi || k > n || !(z > 0.0)) return aeb::fail(AEB_EINVAL, "aeb_wilson: bad argument");
-    if (n == 0) {
-        *lo = 0.0;
-        *hi = 1.0;
-        return AEB_OK;
-    }
-    const double nn = (double)n, p = (double)k / nn, z2 = z * z;
-    const double den = 1.0 + z2 / nn;
-    const double centre = (p + z2 / (2.0 * nn)) / den;
-    const double half = z * std::sqrt(p * (1.0 - p) / nn + z2 / (4.0 * nn * nn)) / den;
-    *lo = centre - half;
-    *hi = centre + half;
-    return AEB_OK;
-}
-
-namespace {
-
-template <class S>
-void merge_common(S &a, const S &b)
-{
-    a.n += b.n;
-    a.n_stop += b.n_stop;
-    a.n_contact += b.n_contact;
-    a.n_horizon += b.n_horizon;
-    a.n_invalid += b.n_invalid;
-    a.steps += b.steps;
-    a.sum_d += b.sum_d;
-    a.sumsq_d += b.sumsq_d;
-    a.sum_v += b.sum_v;
-    a.sumsq_v += b.sumsq_v;
-    a.min_d = std::fmin(a.min_d, b.min_d);
-    a.max_d = std::fmax(a.max_d, b.max_d);
-    a.min_v = std::fmin(a.min_v, b.min_v);
-    a.max_v = std::fmax(a.max_v, b.max_v);
-}
-
-}  // namespace
-
-extern "C" aeb_status aeb_stats_merge(aeb_stats *acc, const aeb_stats *part)
-{
-    aeb::clear_error();
-    if (!acc || !part) return aeb::fail(AEB_EINVAL, "aeb_stats_merge: NULL argument");
-    if (acc->lo_d != part->lo_d || acc->w_d != part->w_d || acc->lo_v != part->lo_v ||
-        acc->w_v != part->w_v)
-        return aeb::fail(AEB_EINVAL, "aeb_stats_merge: histogram specs differ");
-    merge_common(*acc, *part);
-    for (int j = 0; j < AEB_NBINS; ++j) {
-        acc->hist_d[j] += part->hist_d[j];
-        acc->hist_v[j] += part->hist_v[j];
-    }
-    return AEB_OK;
-}
-
-extern "C" aeb_status aeb_job_stats_merge(aeb_job_stats *acc, const aeb_job_stats *part)
-{
-    aeb::clear_error();
-    if (!acc || !part) return aeb::fail(AEB_EINVAL, "aeb_job_stats_merge: NULL argument");
-    merge_common(*acc, *part);
-    return AEB_OK;
-}
 
 extern "C" aeb_status aeb_ttc_sweep(const aeb_model *model, const aeb_scenario *scenarios,
                                     uint32_t n_scen, uint64_t n_per, const double *thresholds,

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(aeb):
     L = C.CDLL(aeb._build.LIB)
     for n in names:
         assert hasattr(L, n), n
-    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 4
+    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 5
 
 
 def test_struct_layouts_match_header(aeb, tmp_path):
@@ -46,7 +46,9 @@ def test_struct_layouts_match_header(aeb, tmp_path):
                "aeb_hist_spec": aeb.HistSpec, "aeb_stats": aeb.Stats, "aeb_job": aeb.Job,
                "aeb_job_stats": aeb.JobStats, "aeb_launch_config": aeb.LaunchConfig,
                "aeb_serve_cfg": aeb.ServeCfg, "aeb_latency": aeb.Latency,
-               "aeb_serve_counters": aeb.ServeCounters, "aeb_sweep_result": aeb.SweepResult}
+               "aeb_serve_counters": aeb.ServeCounters, "aeb_sweep_result": aeb.SweepResult,
+               "aeb_wstats": aeb.WStats, "aeb_summary": aeb.Summary, "aeb_prob": aeb.Prob,
+               "aeb_is_result": aeb.IsResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for cname, py in structs.items():

@@ -74,7 +74,8 @@ def test_rare_event_plain_vs_importance(aeb):
     cols_q, w = aeb.aeb_sample_params_is(m, p, ai.rare_event_proposal(p), 0, n_is)
     Oq = device_run(aeb, m, cols_q, n_is, aeb.FP32_COMP)
     ws, _ = weighted(aeb, Oq, torch.from_numpy(w).cuda(), n_is, h0)
-    p_is, se_is, (lo, hi) = aeb.is_estimate(ws)
+    r = aeb.aeb_is_estimate(ws)
+    p_is, se_is = r.p, r.se
     assert abs(p_is - p_mc) < 4 * math.hypot(se_is, se_mc), (p_is, se_is, p_mc, se_mc)
     # variance per sample: plain p (1 - p) against the weighted estimator's
     vr = (p_mc * (1 - p_mc)) / (se_is ** 2 * n_is)

@@ -249,6 +249,73 @@ def test_ttc_trigger_step(oracle_mod):
     assert o3["n_onset"][0] == -1
 
 
+def test_ttc_probe_records_and_override(oracle_mod):
+    """The TTC test hook (used to check the binary32 kernel's trigger ties):
+    for a car at constant speed it records x_n = v0 n dt, the measured gap
+    d0 - x_n + noise and thr v0 at every step before the trigger, with the
+    margin positive before the trigger step and not positive at it; forcing
+    the trigger k steps later shifts the stop by v0 k dt (constant
+    deceleration after onset); forcing it never coasts into the lead."""
+    v0, mu, thr, noise, delay = 20.0, 0.8, 1.5, 0.37, 0.15
+    dt = 1e-3
+    d0 = 80.0
+    m = ai.Model(a_cmd=-15.0, lead=1, trigger=1, ttc_thr=thr)
+    p = one([(v0, d0, mu, 0.0, 1500.0, 0.0, 0.0, delay, noise)])
+    n_t = math.ceil((d0 + noise - thr * v0) / (v0 * dt))
+    nd = math.ceil(delay / dt - 1e-9)
+    out, rec = oracle_mod.rollout_probe(m, p, 0, force=-2, lo=0, hi=n_t + 50)
+    ref = oracle_mod.rollout(m, p)
+    for k in out:
+        assert out[k] == ref[k][0] or (math.isnan(out[k]) and math.isnan(ref[k][0])), k
+    assert out["n_onset"] == n_t + nd
+    steps = np.arange(n_t + 1)
+    assert np.allclose(rec["x"][:n_t + 1], v0 * steps * dt, rtol=0, atol=1e-9)
+    assert np.allclose(rec["gap_meas"][:n_t + 1], d0 - v0 * steps * dt + noise, rtol=0, atol=1e-9)
+    assert np.all(rec["thr_closing"][:n_t + 1] == thr * v0)
+    assert np.all(rec["reading"][:n_t + 1] == 1)
+    margin = rec["gap_meas"] - rec["thr_closing"]
+    assert np.all(margin[:n_t] > 0) and margin[n_t] <= 0
+    assert np.all(np.isnan(rec["gap_meas"][n_t + 1:])) and np.all(rec["reading"][n_t + 1:] == -1)
+    same, _ = oracle_mod.rollout_probe(m, p, 0, force=n_t)
+    assert same == out
+    late, _ = oracle_mod.rollout_probe(m, p, 0, force=n_t + 7)
+    assert late["n_onset"] == n_t + 7 + nd and late["status"] == 0
+    r = mu * 9.81
+    assert abs((late["x_ref"] - out["x_ref"]) - v0 * 7 * dt) <= r * dt * dt / 4 + 1e-9
+    never, _ = oracle_mod.rollout_probe(m, p, 0, force=-1)
+    assert never["n_onset"] == -1 and never["status"] == 1 and abs(never["v_imp"] - v0) < 1e-9
+
+
+@pytest.mark.parametrize("case", ["plain", "perception", "moving_lead"])
+def test_ttc_probe_without_override_is_the_rollout(oracle_mod, case):
+    m = ai.ttc_model(thr=2.0)
+    sc = ai.single_scenario(seed=77)
+    if case == "perception":
+        m = ai.replace(m, perc_sigma=0.8, perc_drop=0.2, perc_latency=0.05, perc_seed=5)
+    elif case == "moving_lead":
+        m = ai.replace(ai.lead_braking_model(lead_decel=4.0), trigger=1, ttc_thr=3.0)
+        sc = ai.lead_braking_scenario(seed=78)
+    n = 40
+    p = oracle_mod.sample(m, sc, 0, n)
+    ref = oracle_mod.rollout(m, p, row0=1000)
+    for i in range(n):
+        out, rec = oracle_mod.rollout_probe(m, p, i, row=1000 + i, lo=0, hi=20_000)
+        for k in out:
+            assert out[k] == ref[k][i], (i, k)
+        tested = rec["reading"] >= 0
+        margin = rec["gap_meas"] - rec["thr_closing"]
+        fired = tested & (rec["reading"] == 1) & (margin <= 0)
+        if ref["n_onset"][i] >= 0:
+            # the first step whose present reading has a non-positive margin
+            lat = oracle_mod.steps_to_reach(m.perc_latency, m.dt) if case == "perception" else 0
+            n_t = int(np.argmax(fired))
+            assert fired.any() and ref["n_onset"][i] == n_t + lat + \
+                oracle_mod.steps_to_reach(p["t_delay"][i], m.dt)
+            assert not tested[n_t + 1:].any()
+        else:
+            assert not fired.any()
+
+
 # ---------------------------------------------------------------------------
 # Realised deceleration: brute-force fixed point of the force balance
 # ---------------------------------------------------------------------------

@@ -3,7 +3,7 @@ mistake in a copy of the oracle source (on the CPU, in a temporary directory),
 builds it, and runs the oracle pin tests against that build in a child
 process: at least one pin has to fail.  The C cases mutate the C oracle; the
 Python cases mutate the package's own statistics (interval, quantile,
-exceedance, importance-sampling estimate)."""
+exceedance, importance-sampling estimate, moments)."""
 import os
 import shutil
 import subprocess
@@ -26,8 +26,8 @@ MUTATIONS = [
     ("Eq. 5 sign", "c->cap = (mu * m->g) / (1.0 + mh);", "c->cap = (mu * m->g) / (1.0 - mh);"),
     ("no stop refinement", "double s = v / (v - vn);", "double s = 1.0;"),
     ("actuator stage", "ka2 = (u - a2) * c->it;", "ka2 = (u - a1) * c->it;"),
-    ("TTC threshold", "if (reading && gap_meas <= m->ttc_thr * closing)",
-     "if (reading && gap_meas < m->ttc_thr * closing - 0.01)"),
+    ("TTC threshold", "int fire = reading && gap_meas <= m->ttc_thr * closing;",
+     "int fire = reading && gap_meas < m->ttc_thr * closing - 0.01;"),
     ("onset rounding", "c->n_delay = om_steps_to_reach(td, m->dt);",
      "c->n_delay = (int64_t)(td / m->dt);"),
     ("impact speed", "*v_imp = v + s * (vn - v);", "*v_imp = vn;"),
@@ -72,6 +72,8 @@ PY_MUTATIONS = [
     ("exceedance at the headway", "np.asarray(values) > h", "np.asarray(values) >= h"),
     ("IS variance centring", "var = (math.fsum(y * y) - n * p * p) / (n - 1)",
      "var = math.fsum(y * y) / (n - 1)"),
+    ("biased standard deviation", "math.sqrt(math.fsum(r * r) / (k - 1))",
+     "math.sqrt(math.fsum(r * r) / k)"),
 ]
 
 PIN_TESTS = ("test_oracle_rng.py", "test_oracle_model.py", "test_oracle_stats.py",

@@ -112,6 +112,22 @@ def test_quantile_definition(oracle_mod):
             assert oracle_mod.quantile(x, q) == np.quantile(x, q, method="inverted_cdf")
 
 
+def test_moments_closed_forms(oracle_mod):
+    """The arithmetic sequence a + d j, j = 0 .. n-1 (every value and the
+    sums exact in binary64) has mean a + d (n - 1) / 2 and unbiased variance
+    d^2 n (n + 1) / 12; an offset far above the spread must not disturb the
+    spread (two passes)."""
+    for a, d, n in ((0.0, 1.0, 2), (3.0, 0.5, 7), (-40.0, 0.25, 1000), (1e8, 1.0, 101)):
+        x = a + d * np.arange(n, dtype=np.float64)
+        m, sd = oracle_mod.moments(x)
+        assert m == a + d * (n - 1) / 2
+        assert math.isclose(sd, math.sqrt(d * d * n * (n + 1) / 12.0), rel_tol=1e-14)
+    m, sd = oracle_mod.moments([5.0])
+    assert m == 5.0 and math.isnan(sd)
+    m, sd = oracle_mod.moments([])
+    assert math.isnan(m) and math.isnan(sd)
+
+
 def test_exceedance(oracle_mod):
     x = np.array([1.0, 2.0, 3.0, 4.0])
     assert oracle_mod.exceedance(x, 2.0, 4) == 0.5

@@ -3,19 +3,38 @@ seeded inputs.
 
   * AEB_FP64_PLAIN must equal the oracle in every bit of every output
     (Sec. V-D / VI-A: maximum deviation 0.000000 m between CPU and GPU).
-  * AEB_FP32_COMP must stay within the stated tolerances:
+  * AEB_FP32_COMP must stay within the stated tolerances, for every output:
       - stopped in both: |x_ref - x_ref64| <= 1e-5 x_ref64 (relative);
       - stop/contact flag may differ only where the path that stopped has
-        |d0 - x_ref| < 1e-3 m; such samples are counted;
-      - TTC trigger: the onset step may differ (the trigger is a threshold on
-        a state the two precisions carry with different rounding); such
-        samples are counted and reported, the others meet the bounds above;
+        |final gap| < 1e-3 m; such samples are counted;
       - stopped: t_end within 1e-6 s + 1e-6 relative;
       - contact: the contact instant and speed are as well conditioned as the
         position allows, so the bound is the position bound carried through
         the kinematics: |dt_end| v_imp <= 1e-5 d0 and
         |dv_imp| v_imp <= r_max 1e-5 d0 (r_max = 10 m/s^2 bounds |dv/dt|);
-      - horizon: t_end identical.
+      - horizon: t_end identical;
+      - n_steps equal, or one apart where the end falls on a step boundary
+        (stop: t_end within the stop bound of the boundary; contact: within
+        the contact bound); x_raw (the paper's D_stop = x(t_stop), Eq. 3)
+        within 1e-5 relative, plus where n_steps is one apart the travel of
+        that step (stop: <= r_max dt^2, the speed there is below r_max dt;
+        contact: <= dt (v_imp + v_lead + r_max dt));
+      - brake onset identical in immediate mode (an integer computed in
+        binary64 from the same rule).  Under the TTC trigger the onset may
+        differ only where the trigger decision is a rounding tie, proven per
+        sample: at the step where the binary32 kernel fired and the oracle did
+        not, the oracle's binary64 margin (gap + noise) - thr closing speed is
+        <= eps; at every step where the oracle fired and the kernel did not,
+        the margin is >= -eps (or the reading's dropout decision is a tie:
+        |u4 - perc_drop| <= 2^-23).  eps = 2^-21 (|gap + noise| + thr |closing|
+        + x_n + d0 + x_L + thr v_L) + 12 2^-24 perc_sigma: eight binary32
+        ulps of every quantity the kernel rounds on the way to the margin (the
+        compensated state carries <= ~6 ulps of position through the approach,
+        each operand of the margin one rounding, the lead's closed form in
+        binary32 about three, the reading's 24-bit uniforms 6 2^-24 sigma
+        plus its arithmetic).  Such a sample is then compared, with every
+        bound above, against the oracle run with its trigger forced to the
+        kernel's step: no sample escapes the bounds.
   * aeb_reduce: integer counts and histograms exact, extremes exact, sums
     within n * 2^-52 * sum|x| of the exactly rounded sum.
 """
@@ -25,6 +44,7 @@ import numpy as np
 import pytest
 
 import aeb_inputs as ai
+from fp32_bounds import fp32_report, resolve_onset_ties, with_gap
 
 pytestmark = pytest.mark.gpu
 
@@ -140,65 +160,6 @@ def test_zero_samples_and_tiny_horizon(aeb, oracle_mod):
     aeb.aeb_rollout(ai.single_model(), P, 0, aeb.FP64_PLAIN, aeb.alloc_outputs(1))
 
 
-def fp32_report(m, got, exp):
-    """Compare FP32-compensated outputs with the binary64 ones; return counts
-    of tolerated disagreements and the worst errors, asserting the bounds."""
-    s32, s64 = got["status"], exp["status"]
-    d0 = None
-    on_diff = got["n_onset"] != exp["n_onset"]
-    if m.trigger == ai.TRIGGER_IMMEDIATE:
-        assert not np.any(on_diff), "onset step must match in immediate mode"
-    flag_diff = (s32 != s64) & ~on_diff
-    rep = {"n": len(s32), "onset_disagree": int(on_diff.sum()), "flag_disagree": int(flag_diff.sum())}
-    if flag_diff.any():
-        # whichever path stopped must have stopped within 1e-3 m of the lead
-        idx = np.nonzero(flag_diff)[0]
-        stopped_gap = np.where(s64[idx] == 0, exp["gap"][idx], got["gap"][idx])
-        assert np.all(np.abs(stopped_gap) < 1e-3), stopped_gap
-    same = (s32 == s64) & ~on_diff
-    st = same & (s64 == 0)
-    rel = np.abs(got["x_ref"][st] - exp["x_ref"][st]) / np.maximum(np.abs(exp["x_ref"][st]), 1e-3)
-    rep["x_ref_rel_max"] = float(rel.max()) if rel.size else 0.0
-    rep["x_ref_rel_mean"] = float(rel.mean()) if rel.size else 0.0
-    assert rep["x_ref_rel_max"] <= 1e-5, rep
-    ct = same & (s64 == 1)
-    if ct.any():
-        vi = exp["v_imp"][ct]
-        d0 = exp["x_ref"][ct]
-        dv = np.abs(got["v_imp"][ct] - vi)
-        dtc = np.abs(got["t_end"][ct] - exp["t_end"][ct])
-        rep["v_imp_abs_max"] = float(dv.max())
-        rep["contact_dt_x_v_over_d0_max"] = float((dtc * vi / d0).max())
-        rep["contact_dv_x_v_over_d0_max"] = float((dv * vi / d0).max())
-        assert np.all(dtc * vi <= 1e-5 * d0), rep
-        assert np.all(dv * vi <= 10.0 * 1e-5 * d0), rep
-    sp = same & (s64 == 0)
-    dts = np.abs(got["t_end"][sp] - exp["t_end"][sp])
-    rep["stop_t_end_abs_max"] = float(dts.max()) if dts.size else 0.0
-    assert np.all(dts <= 1e-6 + 1e-6 * exp["t_end"][sp]), rep
-    hz = same & (s64 == 2)
-    assert np.array_equal(got["t_end"][hz], exp["t_end"][hz])
-    return rep
-
-
-def lead_pos(m, t):
-    """Closed-form position of the braking lead at times t (numpy)."""
-    if m.lead_decel > 0.0:
-        ts = m.lead_v0 / m.lead_decel
-        return np.where(t >= ts, 0.5 * m.lead_v0 * ts, t * (m.lead_v0 - 0.5 * m.lead_decel * t))
-    return t * m.lead_v0
-
-
-def with_gap(out, p, m):
-    """The gap to the lead where each rollout ended (inf without a lead)."""
-    out = dict(out)
-    if not m.lead:
-        out["gap"] = np.full(len(out["x_ref"]), np.inf)
-    else:
-        out["gap"] = (p["d0"] + lead_pos(m, out["t_end"])) - out["x_ref"]
-    return out
-
-
 FP32_CASES = {
     "single_scenario": (ai.single_model(), ai.single_scenario(seed=10), 20_000),
     "paper_preset": (ai.paper_model(), ai.paper_scenario(seed=11), 10_000),
@@ -234,12 +195,14 @@ FP32_CASES = {
 def test_fp32_comp_within_tolerance(aeb, oracle_mod, name):
     m, sc, n = FP32_CASES[name]
     p = ai.draw_params(m, sc, n)
-    exp = with_gap(oracle_mod.rollout(m, p, threads=8), p, m)
-    got = with_gap(gpu_rollout(aeb, m, p, aeb.FP32_COMP), p, m)
-    rep = fp32_report(m, got, exp)
+    exp = oracle_mod.rollout(m, p, threads=8)
+    got = gpu_rollout(aeb, m, p, aeb.FP32_COMP)
+    exp, ties = resolve_onset_ties(oracle_mod, m, p, np.arange(n), got, exp)
+    rep = fp32_report(m, with_gap(got, p, m), with_gap(exp, p, m), ties)
     print(name, rep)
-    if m.trigger == ai.TRIGGER_TTC:
-        assert rep["onset_disagree"] <= max(3, 1e-3 * n), rep
+    # every tie is proven above; many of them would point at a drift of the
+    # kernel's margin, not at rounding
+    assert rep["onset_ties"] <= max(3, 1e-3 * n), rep
 
 
 def test_reduce_against_oracle(aeb, oracle_mod):
