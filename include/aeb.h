@@ -222,6 +222,10 @@ typedef struct aeb_serve_cfg {
     int32_t max_waves_in_flight;  /* waves queued on the GPU at once (1..4)           */
     int32_t sampler_threads;      /* host sampling threads (<= 0: all)                */
     uint64_t max_request_samples; /* larger requests are rejected (<= arena_rows)     */
+    int32_t wave_timeout_ms;      /* watchdog: a wave not complete this long after its
+                                     launch fails its requests with AEB_ETIMEOUT
+                                     (0: 10,000 ms; < 0: no watchdog)                 */
+    int32_t reserved;             /* must be 0                                        */
 } aeb_serve_cfg;
 
 /* Per-request timing, milliseconds. */
@@ -235,7 +239,20 @@ typedef struct aeb_latency {
 /* Engine counters since creation. */
 typedef struct aeb_serve_counters {
     uint64_t submitted, completed, cancelled, failed, rollouts, waves;
+    uint64_t timed_out;   /* failed requests that the wave watchdog ended       */
+    uint64_t rows_free;   /* arena rows not held by any request (now)           */
 } aeb_serve_counters;
+
+/* Host-side fault injection into a serving engine, for testing its failure
+ * handling without any GPU fault (aeb_serve_inject_faults).  Counts are
+ * 1-based from the call (0: no fault); each fires once. */
+typedef struct aeb_serve_faults {
+    uint64_t fail_admission;        /* the k-th admission finds no rows: AEB_ENOMEM     */
+    uint64_t fail_wave_launch;      /* the k-th wave's launch reports a CUDA error      */
+    uint64_t fail_wave_completion;  /* the k-th wave launched completes with an error   */
+    int32_t hold_waves_ms;          /* every wave's completion is seen this late (>= 0) */
+    int32_t reserved;               /* must be 0                                        */
+} aeb_serve_faults;
 
 /* Opaque serving engine. */
 typedef struct aeb_server aeb_server;
@@ -506,8 +523,12 @@ aeb_status aeb_serve_submit(aeb_server *srv, const aeb_scenario *scenario, uint6
 /*
  * Wait up to timeout_ms (0: do not wait, < 0: no limit) for a request.  On
  * AEB_OK the statistics and latency are written and the ticket is released.
- * AEB_EAGAIN (timeout_ms == 0) or AEB_ETIMEOUT if still running,
- * AEB_ECANCELLED if cancelled, AEB_EINVAL for an unknown ticket.  Thread-safe.
+ * AEB_EAGAIN (timeout_ms == 0) or AEB_ETIMEOUT if still running (the ticket
+ * stays valid), AEB_ECANCELLED if cancelled, AEB_EINVAL for an unknown ticket.
+ * A failed request releases its ticket and returns its error: AEB_ENOMEM (no
+ * arena rows could be granted), AEB_ECUDA (a wave holding one of its chunks
+ * failed), AEB_ETIMEOUT (the wave watchdog, see wave_timeout_ms; the message
+ * says which).  Thread-safe.
  */
 aeb_status aeb_serve_poll(aeb_server *srv, uint64_t ticket, int32_t timeout_ms,
                           aeb_job_stats *stats, aeb_latency *lat);
@@ -518,6 +539,19 @@ aeb_status aeb_serve_cancel(aeb_server *srv, uint64_t ticket);
 
 /* Engine counters (thread-safe snapshot). */
 aeb_status aeb_serve_counters_get(aeb_server *srv, aeb_serve_counters *out);
+
+/*
+ * aeb_serve_inject_faults -- make the engine's next admissions or waves fail
+ * on the host, to test the failure handling (no GPU fault is made: an
+ * injected launch error skips the launch, an injected completion error or
+ * hold replaces what the wave's finished event reports).  The paper has no
+ * counterpart; it supports the serving loop of Sec. VI-F.  Whatever fails, a
+ * failed request's queued chunks are dropped and its arena rows return once
+ * none of its chunks is on the GPU (counters.rows_free shows them back);
+ * other requests carry on.  Replaces any earlier injection.  Thread-safe.
+ * AEB_EINVAL: NULL argument, hold_waves_ms < 0, reserved != 0.
+ */
+aeb_status aeb_serve_inject_faults(aeb_server *srv, const aeb_serve_faults *faults);
 
 /* Stop the engine after the work in flight, release everything (NULL: no-op). */
 void aeb_serve_destroy(aeb_server *srv);

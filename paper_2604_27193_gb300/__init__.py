@@ -101,7 +101,8 @@ class ServeCfg(C.Structure):
     _fields_ = [("precision", C.c_int32), ("device", C.c_int32), ("arena_rows", C.c_uint64),
                 ("chunk_samples", C.c_uint64), ("wave_samples", C.c_uint64),
                 ("max_waves_in_flight", C.c_int32), ("sampler_threads", C.c_int32),
-                ("max_request_samples", C.c_uint64)]
+                ("max_request_samples", C.c_uint64), ("wave_timeout_ms", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Latency(C.Structure):
@@ -110,7 +111,13 @@ class Latency(C.Structure):
 
 class ServeCounters(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "cancelled", "failed",
-                                          "rollouts", "waves")]
+                                          "rollouts", "waves", "timed_out", "rows_free")]
+
+
+class ServeFaults(C.Structure):
+    _fields_ = [("fail_admission", C.c_uint64), ("fail_wave_launch", C.c_uint64),
+                ("fail_wave_completion", C.c_uint64), ("hold_waves_ms", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class SweepResult(C.Structure):
@@ -195,6 +202,7 @@ def lib():
                                          P(Latency)]
             L.aeb_serve_cancel.argtypes = [C.c_void_p, C.c_uint64]
             L.aeb_serve_counters_get.argtypes = [C.c_void_p, P(ServeCounters)]
+            L.aeb_serve_inject_faults.argtypes = [C.c_void_p, P(ServeFaults)]
             L.aeb_serve_destroy.argtypes = [C.c_void_p]
             L.aeb_serve_destroy.restype = None
             L.aeb_stats_summary.argtypes = [P(Stats), P(Summary)]
@@ -209,7 +217,8 @@ def lib():
                        "aeb_serve_create", "aeb_serve_submit", "aeb_serve_poll",
                        "aeb_serve_cancel", "aeb_serve_counters_get", "aeb_sample_params_is",
                        "aeb_reduce_weighted", "aeb_stats_summary", "aeb_job_stats_summary",
-                       "aeb_hist_quantile", "aeb_hist_exceedance", "aeb_is_estimate"):
+                       "aeb_hist_quantile", "aeb_hist_exceedance", "aeb_is_estimate",
+                       "aeb_serve_inject_faults"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != ABI_VERSION:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -446,9 +455,11 @@ class Server:
     def __init__(self, m, precision: int = FP32_COMP, device: int = 0,
                  arena_rows: int = 1 << 22, chunk_samples: int = 1 << 18,
                  wave_samples: int = 1 << 21, max_waves_in_flight: int = 2,
-                 sampler_threads: int = 0, max_request_samples: int = 1_000_000):
+                 sampler_threads: int = 0, max_request_samples: int = 1_000_000,
+                 wave_timeout_ms: int = 0):
         cfg = ServeCfg(precision, device, arena_rows, chunk_samples, wave_samples,
-                       max_waves_in_flight, sampler_threads, max_request_samples)
+                       max_waves_in_flight, sampler_threads, max_request_samples,
+                       wave_timeout_ms, 0)
         self._h = C.c_void_p()
         ms = model(m)
         _check(lib().aeb_serve_create(C.byref(cfg), C.byref(ms), C.byref(self._h)))
@@ -460,7 +471,8 @@ class Server:
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = -1):
-        """(status, JobStats, Latency); status OK, EAGAIN, ETIMEOUT or ECANCELLED."""
+        """(status, JobStats, Latency); status OK, EAGAIN, ETIMEOUT or ECANCELLED
+        (other failures raise AebError)."""
         st, lat = JobStats(), Latency()
         code = lib().aeb_serve_poll(self._h, ticket, timeout_ms, C.byref(st), C.byref(lat))
         if code not in (OK, EAGAIN, ETIMEOUT, ECANCELLED):
@@ -474,6 +486,12 @@ class Server:
         c = ServeCounters()
         _check(lib().aeb_serve_counters_get(self._h, C.byref(c)))
         return c
+
+    def inject_faults(self, fail_admission: int = 0, fail_wave_launch: int = 0,
+                      fail_wave_completion: int = 0, hold_waves_ms: int = 0):
+        """aeb_serve_inject_faults (host-side failures for tests)."""
+        f = ServeFaults(fail_admission, fail_wave_launch, fail_wave_completion, hold_waves_ms, 0)
+        _check(lib().aeb_serve_inject_faults(self._h, C.byref(f)))
 
     def close(self):
         if self._h:

@@ -104,6 +104,9 @@ LaunchCfg launch_cfg(aeb_precision precision);
 void set_launch_cfg(aeb_precision precision, const LaunchCfg &cfg);
 aeb_status check_model(const aeb_model *m, ModelDev *out);
 aeb_status check_params(const aeb_params *p, ParamsDev *out);
+// A histogram spec: finite origins, widths positive powers of two (AEB_EINVAL
+// with a message otherwise); shared by every reduction entry point.
+aeb_status check_hist(const aeb_hist_spec *h);
 OutDev out_dev(const aeb_outputs *o);
 aeb_status cuda_fail(cudaError_t e, const char *what);
 

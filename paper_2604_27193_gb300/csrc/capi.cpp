@@ -117,8 +117,6 @@ aeb_status check_params(const aeb_params *p, ParamsDev *out)
     return AEB_OK;
 }
 
-namespace {
-
 aeb_status check_hist(const aeb_hist_spec *h)
 {
     if (!h) return fail(AEB_EINVAL, "hist spec is NULL");
@@ -128,8 +126,6 @@ aeb_status check_hist(const aeb_hist_spec *h)
         return fail(AEB_EINVAL, "hist width must be a positive power of two");
     return AEB_OK;
 }
-
-}  // namespace
 
 OutDev out_dev(const aeb_outputs *o)
 {

@@ -15,7 +15,6 @@
 // caller.  Every call overwrites the partials it uses before reading them, and
 // the histogram bins it accumulates into are in the caller's aeb_stats, which
 // the call clears first, so nothing from an earlier call leaks into a result.
-#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -37,12 +36,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 RedPartial *g_partials_addr[kMaxDevices];  // device address per device ordinal
 
-bool pow2(double w)
-{
-    int ex = 0;
-    return w > 0.0 && std::isfinite(w) && std::frexp(w, &ex) == 0.5;
-}
-
 }  // namespace
 }  // namespace aeb
 
@@ -52,7 +45,7 @@ extern "C" aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n,
 {
     using namespace aeb;
     clear_error();
-    if (!out || !stats || !hist) return fail(AEB_EINVAL, "aeb_reduce_noalloc: NULL argument");
+    if (!out || !stats) return fail(AEB_EINVAL, "aeb_reduce_noalloc: NULL argument");
     if (n > AEB_REDUCE_NOALLOC_MAX_N)
         return fail(AEB_EINVAL, "aeb_reduce_noalloc: n = " + std::to_string(n) +
                                     " exceeds the limit of its fixed scratch (" +
@@ -62,10 +55,8 @@ extern "C" aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n,
         return fail(AEB_EINVAL, "aeb_reduce_noalloc: status, x_ref, v_imp and n_steps are required");
     if (reinterpret_cast<uintptr_t>(stats) % 8 != 0)
         return fail(AEB_EINVAL, "aeb_reduce_noalloc: stats is not 8-byte aligned");
-    if (!std::isfinite(hist->lo_d) || !std::isfinite(hist->lo_v) || !pow2(hist->w_d) ||
-        !pow2(hist->w_v))
-        return fail(AEB_EINVAL, "aeb_reduce_noalloc: hist origin must be finite and widths "
-                                "positive powers of two");
+    aeb_status st = check_hist(hist);  // the same rule as aeb_reduce
+    if (st != AEB_OK) return st;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

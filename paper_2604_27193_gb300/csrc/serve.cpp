@@ -17,6 +17,17 @@
 // Because chunks are fixed pieces of a request and each is reduced in a fixed
 // order, a request's statistics are the same bits whatever it shares waves
 // with.  The GPU never waits on the host: every wave is a bounded launch.
+//
+// Failures.  A request fails when its rows cannot be granted (AEB_ENOMEM),
+// its sampling or upload fails, a wave holding one of its chunks fails to
+// launch or completes with an error (AEB_ECUDA), or such a wave has not
+// completed wave_timeout_ms after its launch (the watchdog: AEB_ETIMEOUT).
+// A failed request's queued chunks are dropped, and its rows return to the
+// arena once none of its chunks is on the GPU any more (a timed-out wave keeps
+// its rows until it completes), so that no later request's upload or rollout
+// can overlap work still writing those rows.  Other requests carry on.
+// Failures can be injected on the host (aeb_serve_inject_faults) to test
+// these paths without any GPU fault.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -92,8 +103,10 @@ struct Req {
     uint64_t n = 0;
     RState state = RState::Pending;
     bool cancel = false;
+    bool rows_held = false;    // rows [row0, row0 + n) granted and not yet returned
     uint64_t row0 = 0;
     uint32_t n_chunks = 0, chunks_done = 0;
+    uint32_t inflight = 0;     // chunks in waves the GPU has not finished
     std::vector<aeb_job_stats> chunk;
     cudaEvent_t up_evt = nullptr;
     Clock::time_point t_submit, t_admit, t_ready, t_done;
@@ -114,6 +127,9 @@ struct Wave {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
+    bool timed_out = false;       // the watchdog has failed this wave's requests
+    bool inject_error = false;    // report this wave's completion as a CUDA error
+    Clock::time_point t_launch;
     std::vector<ChunkRef> chunks;
     // device and pinned sub-buffers
     unsigned long long *counter = nullptr;
@@ -125,6 +141,16 @@ struct Wave {
 };
 
 constexpr uint32_t kMaxJobsPerWave = 4096;
+constexpr int32_t kDefaultWaveTimeoutMs = 10000;
+
+// Host-side fault injection (tests of the failure paths): the k-th admission,
+// wave launch or wave completion counted from the injection fails; a delay
+// holds every wave's completion back.
+struct Faults {
+    uint64_t admissions = 0, launches = 0, completions = 0;       // counts so far
+    uint64_t admission_at = 0, launch_at = 0, completion_at = 0;  // 0: none
+    int32_t delay_ms = 0;
+};
 
 void combine(aeb_job_stats &acc, const aeb_job_stats &c)
 {
@@ -179,22 +205,63 @@ struct aeb_server {
     bool stop = false;
     bool feeder_done = false;  // the feeder has left its loop (nothing more to upload)
     aeb_serve_counters counters{};
+    uint64_t rows_free = 0;
+    int32_t wave_timeout_ms = kDefaultWaveTimeoutMs;  // < 0: no watchdog
+    Faults faults;
     std::thread feeder, scheduler;
 
     void run_feeder();
     void run_scheduler();
     bool launch_wave(Wave &w);
-    void finish_wave(Wave &w);
+    void finish_wave(Wave &w, bool ok);
+    void retire_chunk(const ChunkRef &c, const aeb_job_stats *st, Clock::time_point now);
     void finish_request(const ReqP &r, Clock::time_point now);
     void fail_request(const ReqP &r, aeb_status code);
+    void release_rows(const ReqP &r);
 };
 
+// Return a request's rows to the arena (once).
+void aeb_server::release_rows(const ReqP &r)
+{
+    if (!r->rows_held) return;
+    rows.release(r->row0, r->n);
+    rows_free += r->n;
+    r->rows_held = false;
+    cv_feed.notify_all();
+}
+
+// End a request with an error (once): its queued chunks are dropped; its rows
+// return now if none of its chunks is on the GPU, else when the last retires.
 void aeb_server::fail_request(const ReqP &r, aeb_status code)
 {
+    if (r->state == RState::Done || r->state == RState::Cancelled || r->state == RState::Failed)
+        return;
     r->state = RState::Failed;
     r->err = code;
     counters.failed++;
+    if (code == AEB_ETIMEOUT) counters.timed_out++;
+    for (auto it = ready.begin(); it != ready.end();)
+        it = (it->req == r) ? ready.erase(it) : std::next(it);
+    if (r->inflight == 0) release_rows(r);
     cv_done.notify_all();
+}
+
+// A chunk's wave has finished on the GPU (st: its statistics, or NULL if the
+// wave failed).
+void aeb_server::retire_chunk(const ChunkRef &c, const aeb_job_stats *st, Clock::time_point now)
+{
+    const ReqP &r = c.req;
+    r->inflight--;
+    if (r->state == RState::Ready) {
+        if (!st) {
+            fail_request(r, AEB_ECUDA);
+            return;
+        }
+        r->chunk[c.index] = *st;
+        if (++r->chunks_done == r->n_chunks) finish_request(r, now);
+    } else if (r->state == RState::Failed && r->inflight == 0) {
+        release_rows(r);
+    }
 }
 
 void aeb_server::finish_request(const ReqP &r, Clock::time_point now)
@@ -206,14 +273,13 @@ void aeb_server::finish_request(const ReqP &r, Clock::time_point now)
     r->result = acc;
     r->t_done = now;
     r->state = r->cancel ? RState::Cancelled : RState::Done;
-    rows.release(r->row0, r->n);
+    release_rows(r);
     if (r->cancel)
         counters.cancelled++;
     else
         counters.completed++;
     counters.rollouts += r->n;
     cv_done.notify_all();
-    cv_feed.notify_all();
 }
 
 void aeb_server::run_feeder()
@@ -242,8 +308,18 @@ void aeb_server::run_feeder()
                         r = pending.front();
                         pending.pop_front();
                         r->row0 = r0;
-                        r->state = RState::Sampling;
+                        r->rows_held = true;
+                        rows_free -= r->n;
                         r->t_admit = Clock::now();
+                        if (++faults.admissions == faults.admission_at) {
+                            // injected: the grant fails as if the memory were gone
+                            faults.admission_at = 0;
+                            release_rows(r);
+                            fail_request(r, AEB_ENOMEM);
+                            r.reset();
+                            continue;
+                        }
+                        r->state = RState::Sampling;
                         break;
                     }
                 }
@@ -263,7 +339,12 @@ void aeb_server::run_feeder()
         if (e == cudaSuccess && st == AEB_OK) e = cudaEventRecord(r->up_evt, copy_stream);
         std::lock_guard<std::mutex> lk(mu);
         if (st != AEB_OK || e != cudaSuccess) {
-            rows.release(r->row0, r->n);
+            if (r->up_evt) {
+                cudaEventDestroy(r->up_evt);
+                r->up_evt = nullptr;
+            }
+            // the copies already queued must end before the rows are reused
+            cudaStreamSynchronize(copy_stream);
             fail_request(r, st != AEB_OK ? st : AEB_ECUDA);
             continue;
         }
@@ -286,6 +367,7 @@ bool aeb_server::launch_wave(Wave &w)
         ready.pop_front();
     }
     if (w.chunks.empty()) return false;
+    for (auto &c : w.chunks) c.req->inflight++;
     const uint32_t T = (uint32_t)lcfg.tile;
     const uint32_t nj = (uint32_t)w.chunks.size();
     uint32_t nt = 0, nr = 0;
@@ -302,7 +384,13 @@ bool aeb_server::launch_wave(Wave &w)
             w.hred[nr++] = TileDesc{f, j, (uint32_t)std::min<uint64_t>(kRedSegment, c.n - f)};
     }
     w.hfirst[nj] = nr;
-    cudaError_t e = cudaMemcpyAsync(w.djobs, w.hjobs, sizeof(JobDev) * nj, cudaMemcpyHostToDevice, w.stream);
+    cudaError_t e = cudaSuccess;
+    if (++faults.launches == faults.launch_at) {  // injected: the launch reports an error
+        faults.launch_at = 0;
+        e = cudaErrorLaunchFailure;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w.djobs, w.hjobs, sizeof(JobDev) * nj, cudaMemcpyHostToDevice, w.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(w.dtiles, w.htiles, sizeof(TileDesc) * nt, cudaMemcpyHostToDevice, w.stream);
     if (e == cudaSuccess)
@@ -331,27 +419,29 @@ bool aeb_server::launch_wave(Wave &w)
                             w.stream);
     if (e == cudaSuccess) e = cudaEventRecord(w.done, w.stream);
     if (e != cudaSuccess) {
-        for (auto &c : w.chunks)
-            if (c.req->state == RState::Ready) fail_request(c.req, AEB_ECUDA);
-        w.chunks.clear();
+        // whatever part of the wave was queued ends before its rows are reused
+        cudaStreamSynchronize(w.stream);
+        finish_wave(w, false);
         return false;
     }
     w.busy = true;
+    w.timed_out = false;
+    w.inject_error = (++faults.completions == faults.completion_at);
+    if (w.inject_error) faults.completion_at = 0;
+    w.t_launch = Clock::now();
     counters.waves++;
     return true;
 }
 
-void aeb_server::finish_wave(Wave &w)
+// The GPU has finished wave w (ok: without error): retire its chunks.
+void aeb_server::finish_wave(Wave &w, bool ok)
 {
     const Clock::time_point now = Clock::now();
-    for (size_t j = 0; j < w.chunks.size(); ++j) {
-        ChunkRef &c = w.chunks[j];
-        if (c.req->state != RState::Ready) continue;
-        c.req->chunk[c.index] = w.hstats[j];
-        if (++c.req->chunks_done == c.req->n_chunks) finish_request(c.req, now);
-    }
+    for (size_t j = 0; j < w.chunks.size(); ++j) retire_chunk(w.chunks[j], ok ? &w.hstats[j] : nullptr, now);
     w.chunks.clear();
     w.busy = false;
+    w.timed_out = false;
+    w.inject_error = false;
 }
 
 void aeb_server::run_scheduler()
@@ -372,8 +462,11 @@ void aeb_server::run_scheduler()
             r->up_evt = nullptr;
             progress = true;
             if (q != cudaSuccess) {
-                rows.release(r->row0, r->n);
                 fail_request(r, AEB_ECUDA);
+                continue;
+            }
+            if (r->state != RState::Uploading) {  // failed meanwhile
+                release_rows(r);
                 continue;
             }
             r->state = RState::Ready;
@@ -385,21 +478,27 @@ void aeb_server::run_scheduler()
                 ready.push_back(ChunkRef{r, c, c * C, std::min<uint64_t>(C, r->n - c * C)});
         }
         bool any_busy = false;
+        const Clock::time_point now = Clock::now();
         for (auto &w : waves) {
             if (!w.busy) continue;
-            const cudaError_t q = cudaEventQuery(w.done);
+            cudaError_t q = cudaEventQuery(w.done);
+            if (q == cudaSuccess && faults.delay_ms > 0 &&
+                now < w.t_launch + std::chrono::milliseconds(faults.delay_ms))
+                q = cudaErrorNotReady;  // injected: completion held back
+            if (q == cudaSuccess && w.inject_error) q = cudaErrorLaunchFailure;
             if (q == cudaErrorNotReady) {
                 any_busy = true;
+                if (!w.timed_out && wave_timeout_ms >= 0 &&
+                    now > w.t_launch + std::chrono::milliseconds(wave_timeout_ms)) {
+                    // watchdog: the wave's requests stop waiting; the rows stay
+                    // held until the GPU finishes the wave
+                    w.timed_out = true;
+                    for (auto &c : w.chunks) fail_request(c.req, AEB_ETIMEOUT);
+                    progress = true;
+                }
                 continue;
             }
-            if (q != cudaSuccess) {
-                for (auto &c : w.chunks)
-                    if (c.req->state == RState::Ready) fail_request(c.req, AEB_ECUDA);
-                w.chunks.clear();
-                w.busy = false;
-            } else {
-                finish_wave(w);
-            }
+            finish_wave(w, q == cudaSuccess);
             progress = true;
         }
         while (!ready.empty()) {
@@ -462,7 +561,7 @@ extern "C" aeb_status aeb_serve_create(const aeb_serve_cfg *cfg, const aeb_model
     if (cfg->arena_rows == 0 || cfg->chunk_samples == 0 || cfg->chunk_samples % 64 ||
         cfg->wave_samples < cfg->chunk_samples || cfg->max_waves_in_flight < 1 ||
         cfg->max_waves_in_flight > 4 || cfg->max_request_samples == 0 ||
-        cfg->max_request_samples > cfg->arena_rows)
+        cfg->max_request_samples > cfg->arena_rows || cfg->reserved != 0)
         return fail(AEB_EINVAL, "aeb_serve_create: invalid configuration");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
@@ -500,6 +599,8 @@ extern "C" aeb_status aeb_serve_create(const aeb_serve_cfg *cfg, const aeb_model
     for (int f = 0; f < AEB_NFIELDS; ++f)
         s->hcol[f] = reinterpret_cast<double *>(static_cast<char *>(s->staging) + f * col);
     s->rows.init(R);
+    s->rows_free = R;
+    s->wave_timeout_ms = cfg->wave_timeout_ms == 0 ? kDefaultWaveTimeoutMs : cfg->wave_timeout_ms;
     e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
     // wave slots
     const uint64_t T = (uint64_t)s->lcfg.tile;
@@ -623,7 +724,13 @@ extern "C" aeb_status aeb_serve_poll(aeb_server *srv, uint64_t ticket, int32_t t
     }
     srv->reqs.erase(r->ticket);
     if (r->state == RState::Cancelled) return fail(AEB_ECANCELLED, "aeb_serve_poll: cancelled");
-    if (r->state == RState::Failed) return fail(r->err, "aeb_serve_poll: request failed");
+    if (r->state == RState::Failed)
+        return fail(r->err, r->err == AEB_ETIMEOUT
+                                ? "aeb_serve_poll: a wave of the request did not complete "
+                                  "within wave_timeout_ms"
+                                : (r->err == AEB_ENOMEM ? "aeb_serve_poll: no arena rows for "
+                                                          "the request"
+                                                        : "aeb_serve_poll: request failed"));
     if (stats) *stats = r->result;
     if (lat) {
         lat->queue_ms = ms_between(r->t_submit, r->t_admit);
@@ -652,6 +759,25 @@ extern "C" aeb_status aeb_serve_counters_get(aeb_server *srv, aeb_serve_counters
     if (!srv || !out) return fail(AEB_EINVAL, "aeb_serve_counters_get: NULL argument");
     std::lock_guard<std::mutex> lk(srv->mu);
     *out = srv->counters;
+    out->rows_free = srv->rows_free;
+    return AEB_OK;
+}
+
+extern "C" aeb_status aeb_serve_inject_faults(aeb_server *srv, const aeb_serve_faults *f)
+{
+    clear_error();
+    if (!srv || !f) return fail(AEB_EINVAL, "aeb_serve_inject_faults: NULL argument");
+    if (f->hold_waves_ms < 0 || f->reserved != 0)
+        return fail(AEB_EINVAL, "aeb_serve_inject_faults: hold_waves_ms < 0 or reserved != 0");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        Faults &F = srv->faults;
+        F.admission_at = f->fail_admission ? F.admissions + f->fail_admission : 0;
+        F.launch_at = f->fail_wave_launch ? F.launches + f->fail_wave_launch : 0;
+        F.completion_at = f->fail_wave_completion ? F.completions + f->fail_wave_completion : 0;
+        F.delay_ms = f->hold_waves_ms;
+    }
+    srv->cv_sched.notify_all();
     return AEB_OK;
 }
 

@@ -48,7 +48,7 @@ def test_struct_layouts_match_header(aeb, tmp_path):
                "aeb_serve_cfg": aeb.ServeCfg, "aeb_latency": aeb.Latency,
                "aeb_serve_counters": aeb.ServeCounters, "aeb_sweep_result": aeb.SweepResult,
                "aeb_wstats": aeb.WStats, "aeb_summary": aeb.Summary, "aeb_prob": aeb.Prob,
-               "aeb_is_result": aeb.IsResult}
+               "aeb_is_result": aeb.IsResult, "aeb_serve_faults": aeb.ServeFaults}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for cname, py in structs.items():
