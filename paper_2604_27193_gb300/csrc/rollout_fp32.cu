@@ -68,7 +68,7 @@ constexpr int kTileMax = 256;
 constexpr int kWarps = 4;      // warps per block
 constexpr int kThreads = 32 * kWarps;
 #ifndef AEB_FP32_WINDOW
-#define AEB_FP32_WINDOW 16     // steps a lane runs without termination tests
+#define AEB_FP32_WINDOW 32     // steps a lane runs without termination tests
 #endif
 #ifndef AEB_FP32_MIN_BLOCKS
 #define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
@@ -94,6 +94,9 @@ enum { kNoLead = 0, kLeadStationary = 1, kLeadMoving = 2 };
 
 struct ModelF32 {
     float acmd;
+    // binary32 copies of the constants the tile preparation forms binary32
+    // per-sample values from
+    float rho, area, hl, g, phi_f, beta;
     // moving lead: step, initial speed, deceleration, half of it, stop time,
     // stop position (binary32 copies of the model's values)
     float dt, lv0, lb, lhb, lts, lxs;
@@ -105,6 +108,9 @@ struct ModelF32 {
 };
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
+
+static_assert(AEB_FP32_WINDOW >= 2 && AEB_FP32_WINDOW <= 32,
+              "window lengths are found from five binary digits (<= 31 steps)");
 
 // Relative margin on the actuator threshold of a window: covers the rounding
 // of K - 1 binary32 decays of e and of the power and quotient that form the
@@ -133,8 +139,9 @@ __device__ __forceinline__ float powi(float q)
 // Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
 // warp's shared slab.
 template <int LEAD, bool TTC>
-__device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P, uint64_t start,
-                                          int cnt, double thr, int T, float *tf, int *ti)
+__device__ __forceinline__ void prep_tile(const ModelDev &M, const ModelF32 &F, const ParamsDev &P,
+                                          uint64_t start, int cnt, double thr, int T, float *tf,
+                                          int *ti)
 {
     for (int j = threadIdx.x & 31; j < cnt; j += 32) {
         const uint64_t i = start + j;
@@ -153,8 +160,12 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         ti[R_KIND * T + j] = kind;
         if (kind != K_RUN) continue;
         // speed scale s = sqrt(k), bounded below so that a drag-free sample
-        // keeps its scaled state in the normal binary32 range
-        const float k32 = __double2float_rn(((M.rho * f[kCd]) * M.area) / (2.0 * f[kMass]));
+        // keeps its scaled state in the normal binary32 range.  The constants
+        // that end up in binary32 (k, the cap lines, the actuator multipliers)
+        // are formed in binary32 (a few ulps; binary64 division is slow here);
+        // the scales that tie the pairs to metres (sigma, w0, g0) stay binary64.
+        const float k32 = ((F.rho * __double2float_rn(f[kCd])) * F.area) /
+                          (2.0f * __double2float_rn(f[kMass]));
         const float sc = fmaxf(sqrtf(k32), 1e-18f);
         const double sd = (double)sc;
         const float nh6s = __double2float_rn(-(sd * M.h6));
@@ -170,35 +181,35 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
         tf[R_NH2S * T + j] = __double2float_rn(-(sd * M.h2));
         tf[R_NH6S * T + j] = nh6s;
         tf[R_SIGMA * T + j] = __double2float_rn(sigma);
-        const double mu = f[kMu], mh = mu * M.hl;
+        const float mu = __double2float_rn(f[kMu]), mh = mu * F.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
             tf[R_F0 * T + j] = finf();
             tf[R_F1 * T + j] = 0.0f;
             tf[R_R0 * T + j] = finf();
             tf[R_R1 * T + j] = 0.0f;
-            tf[R_MG * T + j] = __double2float_rn((mu * M.g) / (1.0 + mh));
+            tf[R_MG * T + j] = (mu * F.g) / (1.0f + mh);
         } else {
-            const double mg = mu * f[kGc], im = 1.0 / (1.0 - mh), ip = 1.0 / (1.0 + mh);
-            tf[R_F0 * T + j] = __double2float_rn((mg * M.phi_f) * im);
-            tf[R_F1 * T + j] = __double2float_rn((1.0 - M.beta) * im);
-            tf[R_R0 * T + j] = __double2float_rn((mg * (1.0 - M.phi_f)) * ip);
-            tf[R_R1 * T + j] = __double2float_rn(M.beta * ip);
-            tf[R_MG * T + j] = __double2float_rn(mg);
+            const float mg = mu * __double2float_rn(f[kGc]);
+            const float im = 1.0f / (1.0f - mh), ip = 1.0f / (1.0f + mh);
+            tf[R_F0 * T + j] = (mg * F.phi_f) * im;
+            tf[R_F1 * T + j] = (1.0f - F.beta) * im;
+            tf[R_R0 * T + j] = (mg * (1.0f - F.phi_f)) * ip;
+            tf[R_R1 * T + j] = F.beta * ip;
+            tf[R_MG * T + j] = mg;
         }
+        float nmp = -1.0f;
         if (f[kTau] > 0.0) {
-            const double z = M.dt / f[kTau];
-            const double p4 = 1.0 - z + 0.5 * z * z - 0.25 * z * z * z;
-            tf[R_NP2 * T + j] = __double2float_rn(-(1.0 - 0.5 * z));
-            tf[R_NP3 * T + j] = __double2float_rn(-(1.0 - 0.5 * z + 0.25 * z * z));
-            tf[R_NP4 * T + j] = __double2float_rn(-p4);
-            tf[R_NMP * T + j] =
-                __double2float_rn(-(z * (1.0 + z * (-0.5 + z * (1.0 / 6.0 - z / 24.0)))));
+            const float z = F.dt / __double2float_rn(f[kTau]);
+            tf[R_NP2 * T + j] = -(1.0f - 0.5f * z);
+            tf[R_NP3 * T + j] = -(1.0f - 0.5f * z + 0.25f * z * z);
+            tf[R_NP4 * T + j] = -(1.0f - z + 0.5f * z * z - 0.25f * z * z * z);
+            nmp = -(z * (1.0f + z * (-0.5f + z * (1.0f / 6.0f - z / 24.0f))));
         } else {
             tf[R_NP2 * T + j] = 0.0f;
             tf[R_NP3 * T + j] = 0.0f;
             tf[R_NP4 * T + j] = 0.0f;
-            tf[R_NMP * T + j] = -1.0f;
         }
+        tf[R_NMP * T + j] = nmp;
         if (TTC) {  // (g + noise) - thr v scaled by sigma: G + sigma noise - (sigma thr / s) w
             const double ts = thr * (sigma / sd);
             const float tsh = __double2float_rn(ts);
@@ -214,7 +225,7 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ParamsDev &P,
 // stride 32, to keep the step loop's register budget small.
 enum {
     L_F0, L_F1, L_R0, L_R1, L_MG, L_GS, L_U, L_S, L_ETHK, L_NP1, L_NP2, L_NP3, L_NP4,  // floats
-    L_SIGMA,
+    L_SIGMA, L_QF,
     L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI, L_KIDXLO, L_KIDXHI,         // ints
     L_NW_BASE,
     L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NCHK, L_NW_TTC  // TTC trigger only (NCHK: int)
@@ -279,7 +290,7 @@ struct Lane32 {
         // piece if its last step does: e (1 - mP)^(K-1) >= eth (with margin)
         float ethK = eth;
         if (eth > 0.0f) {
-            const float f = powi<AEB_FP32_WINDOW - 1>(1.0f + nmP);
+            const float f = cf(L_QF);  // (1 - mP)^(K-1), taken once per sample
             ethK = (f > 0.0f) ? __fdividef(eth, f) * kMargin : finf();
         }
         set_cf(L_ETHK, ethK);
@@ -297,6 +308,14 @@ struct Lane32 {
     __device__ __forceinline__ int32_t onset() const
     {
         return TTC ? (trig ? ci(L_NB) : -1) : ci(L_NDELAY);
+    }
+
+    // Whether the next step must take the slow path: it crosses a breakpoint
+    // of r(D) (the actuator deviation has reached the piece's threshold) or it
+    // is the horizon's last step (a pending onset is a state change instead).
+    __device__ __forceinline__ bool at_slow(int32_t n_last) const
+    {
+        return n >= n_last || e < eth;
     }
 
     // Next step that must take the slow path: the onset step (if still ahead,
@@ -317,21 +336,38 @@ struct Lane32 {
     // binary32 factor nh6s = -s h6 as the speed update, so distance and speed
     // advance with one step factor (independently rounded factors would scale
     // every stopping distance by their ratio, a systematic ~5e-8 relative
-    // error), and the gap falls by exactly v1 + 2 v2 + 2 v3 + v4.  Returns the
-    // end-of-step low words and actuator deviation.
+    // error), and the gap falls by the stage-speed sum v1 + 2 v2 + 2 v3 + v4,
+    // formed as 6 v1 + s dt (q1 + q2 + q3) (the same sum in exact arithmetic,
+    // one instruction fewer).  Returns the end-of-step low words and actuator
+    // deviation.
     template <bool FULL_MIN>
     __device__ __forceinline__ void rk4_step(float &vl1, float &gl1, float &en) const
     {
         const float v1 = vh + vl;
-        const float q1 = fmaf(v1, v1, FULL_MIN ? rg_full(cf(L_NP1)) : fmaf(e, a1, C));
+        // the four actuator terms C + e a_j are independent of each other and
+        // of the stage chain: two paired binary32 FMAs (per component the same
+        // rounding as fmaf) cost two issue slots instead of four
+        float2 X12, X34;
+        if (FULL_MIN) {
+            X12 = make_float2(rg_full(cf(L_NP1)), rg_full(cf(L_NP2)));
+            X34 = make_float2(rg_full(cf(L_NP3)), rg_full(cf(L_NP4)));
+        } else {
+            const float2 ee = make_float2(e, e), cc = make_float2(C, C);
+            X12 = __ffma2_rn(ee, make_float2(a1, a2), cc);
+            X34 = __ffma2_rn(ee, make_float2(a3, a4), cc);
+        }
+        const float q1 = fmaf(v1, v1, X12.x);
         const float v2 = fmaf(nh2s, q1, v1);
-        const float q2 = fmaf(v2, v2, FULL_MIN ? rg_full(cf(L_NP2)) : fmaf(e, a2, C));
+        const float q2 = fmaf(v2, v2, X12.y);
         const float v3 = fmaf(nh2s, q2, v1);
-        const float q3 = fmaf(v3, v3, FULL_MIN ? rg_full(cf(L_NP3)) : fmaf(e, a3, C));
+        const float q3 = fmaf(v3, v3, X34.x);
         const float v4 = fmaf(ndts, q3, v1);
-        const float q4 = fmaf(v4, v4, FULL_MIN ? rg_full(cf(L_NP4)) : fmaf(e, a4, C));
-        vl1 = fmaf(nh6s, fmaf(2.0f, q2 + q3, q1 + q4), vl);
-        gl1 = gl - fmaf(2.0f, v2 + v3, v1 + v4);
+        const float q4 = fmaf(v4, v4, X34.y);
+        // speed: q1 + 2 q2 + 2 q3 + q4; gap: the stage speeds sum to
+        // v1 + 2 v2 + 2 v3 + v4 = 6 v1 + 2 (nh2s) (q1 + q2 + q3) (ndts = 2 nh2s)
+        const float s23 = q2 + q3, s123 = s23 + q1;
+        vl1 = fmaf(nh6s, fmaf(2.0f, s23, q1 + q4), vl);
+        gl1 = fmaf(-ndts, s123, fmaf(-6.0f, v1, gl));
         en = fmaf(nmP, e, e);
     }
 
@@ -436,6 +472,10 @@ struct Lane32 {
                 const float q2 = q * q, q4 = q2 * q2, q8 = q4 * q4;
                 float r = e;
                 int k = 0;
+                if (AEB_FP32_WINDOW > 16) {
+                    const float q16 = q8 * q8;
+                    if (r * q16 >= m) { r *= q16; k += 16; }
+                }
                 if (r * q8 >= m) { r *= q8; k += 8; }
                 if (r * q4 >= m) { r *= q4; k += 4; }
                 if (r * q2 >= m) { r *= q2; k += 2; }
@@ -629,6 +669,8 @@ struct Lane32 {
         set_cf(L_MG, tf[R_MG * T + slot]);
         set_cf(L_S, tf[R_S * T + slot]);
         set_cf(L_SIGMA, tf[R_SIGMA * T + slot]);
+        // (1 - mP)^(K-1): the actuator decay over a window's last K-1 steps
+        set_cf(L_QF, powi<AEB_FP32_WINDOW - 1>(1.0f + nmP));
         set_ci(L_NDELAY, n_delay);
         set_ci(L_PIDXLO, (int)(uint32_t)pi);
         set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
@@ -648,7 +690,14 @@ struct Lane32 {
         trig = !TTC;
         set_ci(L_NB, TTC ? INT_MAX : n_delay);
         next_event(M.n_max - 1);
-        set_piece(0.0f);
+        // Before onset e = u = 0, so every stage's demand is D = 0, where the
+        // realised deceleration min(D, f0 + f1 D, r0 + r1 D, mu g cos) is 0
+        // (mu >= 0): the stage term r + g sin(theta) is g sin(theta), and no
+        // breakpoint can be reached.  The piece is selected at onset.
+        C = cf(L_GS);
+        a1 = a2 = a3 = a4 = 0.0f;
+        eth = -finf();
+        set_cf(L_ETHK, -finf());
         return false;
     }
 };
@@ -743,11 +792,14 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
         }
         const double d0 = __ldg(P.col[kD0] + pi);
         const double sd = (double)bf[B_S * 32 + j];
-        const double sigma = (sd * sd) / -(double)bf[B_NH6S * 32 + j];
-        const double x0 = d0 - ((double)g0h + (double)g0l) / sigma;
-        const double x1 = d0 - ((double)g1h + (double)g1l) / sigma;
-        const double w0 = ((double)w0h + (double)w0l) / sd;
-        const double w1 = ((double)w1h + (double)w1l) / sd;
+        // back to metres and metres per second: 1 / sigma = -h6 s / s^2 and
+        // 1 / s, one binary64 division each (division is slow in binary64)
+        const double isig = -(double)bf[B_NH6S * 32 + j] / (sd * sd);
+        const double isd = 1.0 / sd;
+        const double x0 = d0 - ((double)g0h + (double)g0l) * isig;
+        const double x1 = d0 - ((double)g1h + (double)g1l) * isig;
+        const double w0 = ((double)w0h + (double)w0l) * isd;
+        const double w1 = ((double)w1h + (double)w1l) * isd;
         const double n = (double)(n1 - 1);
         if (status == AEB_CONTACT && LEAD == kLeadMoving) {
             // gaps and closing speeds to the moving lead at both ends of the step
@@ -818,7 +870,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     tile = nt;
                     cursor = 0;
                     __syncwarp();  // every lane has read its record of the previous tile
-                    prep_tile<LEAD, TTC>(M, P, tile.p0, tile.count, tile.thr, T, tf, ti);
+                    prep_tile<LEAD, TTC>(M, F, P, tile.p0, tile.count, tile.thr, T, tf, ti);
                     __syncwarp();
                 }
                 const unsigned rank = __popc(need & lanemask_lt());
@@ -855,26 +907,30 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         // reach); one vote decides.  Otherwise handle onsets, slow steps and
         // window lengths lane by lane.
         bool full = __all_sync(kFull, !active || L.full_window_ok(tlen));
-        bool slow = false;
         int len = AEB_FP32_WINDOW;
         if (!full) {
             const bool onset = active && L.n == L.ev && L.n < n_last;
             if (__any_sync(kFull, onset)) {  // warp-uniform: once per rollout
                 if (onset) L.onset_event(F, n_last);
             }
-            slow = active && ((L.n == L.ev) || (L.e < L.eth));
-            if (__any_sync(kFull, slow)) {  // warp-uniform: rare
-                if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
-            }
-            if (active && !slow) len = L.window_len(tlen);
+            // a lane already at a slow step runs no window in this pass
+            if (active) len = L.at_slow(n_last) ? 0 : L.window_len(tlen);
             full = __all_sync(kFull, len == AEB_FP32_WINDOW);
         }
-        const bool win = active && !slow;
         bool replay = false;
         if (full) {
-            if (win) replay = L.template step_window<true>(F, len);
+            if (active) replay = L.template step_window<true>(F, len);
         } else {
-            if (win) replay = L.template step_window<false>(F, len);
+            if (active && len > 0) replay = L.template step_window<false>(F, len);
+        }
+        // Slow steps (breakpoint crossings, the horizon's last step) after the
+        // windows: a window that stopped right before one takes it in the same
+        // pass, so the lane does not sit out the next pass's window for one
+        // step.  A lane before its TTC trigger takes one only if it ran no
+        // window in this pass (its trigger test for this step came first).
+        const bool slow = active && !replay && (!TTC || L.trig || len == 0) && L.at_slow(n_last);
+        if (__any_sync(kFull, slow)) {  // warp-uniform: rare
+            if (slow) ended = L.step_slow(F, n_last, vl1, gl1);
         }
         ended = ended || replay;
         const unsigned endm = __ballot_sync(kFull, ended);
@@ -931,6 +987,12 @@ ModelF32 to_f32(const ModelDev &m)
 {
     ModelF32 f;
     f.acmd = (float)m.a_cmd;
+    f.rho = (float)m.rho;
+    f.area = (float)m.area;
+    f.hl = (float)m.hl;
+    f.g = (float)m.g;
+    f.phi_f = (float)m.phi_f;
+    f.beta = (float)m.beta;
     f.dt = (float)m.dt;
     f.lv0 = (float)m.lead_v0;
     f.lb = (float)m.lead_decel;
