@@ -54,12 +54,12 @@ SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
 # DRAM bytes per sample of the FP32 rollout kernel, from one ncu capture at
-# N = 2e6 (183.2 MB per launch); traffic grows in proportion to the samples.
-FP32_TRAFFIC_BYTES_PER_SAMPLE = 183.236864e6 / 2e6
-# binary32 thread instructions the FP32 kernel executes per RK4 lane-step on this
+# N = 2e6 (184.1 MB per launch); traffic grows in proportion to the samples.
+FP32_TRAFFIC_BYTES_PER_SAMPLE = 184.10752e6 / 2e6
+# thread instructions the FP32 kernel executes per RK4 lane-step on this
 # workload (ncu smsp__inst_executed x thread_inst_executed_per_inst_executed at
 # N = 2e6, same profile); the issue-slot view of the roofline
-FP32_THREAD_INST_PER_STEP = 26.9
+FP32_THREAD_INST_PER_STEP = 22.15
 FP32_ISSUE_PEAK = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6  # lane-instructions/s
 
 
@@ -795,8 +795,9 @@ def main():
                      "flops_per_launch": steps_per_launch * FLOPS_PER_STEP,
                      "launch_ms": roll_ms,
                      "note": "flops counted from the 73-op binary64 definition of a step; the "
-                             "kernel runs ~21 fused binary32 instructions per step, so frac "
-                             "may exceed 1 without skipped work",
+                             "kernel runs 18 binary32 instructions per step (12 FFMA, 2 paired "
+                             "FFMA2, 4 FADD), so frac may exceed 1 without skipped work; "
+                             "issue.frac is the headroom measure",
                      "issue": {"thread_inst_per_step": FP32_THREAD_INST_PER_STEP,
                                "achieved": steps_per_launch * FP32_THREAD_INST_PER_STEP
                                            / (roll_ms / 1e3),

@@ -434,7 +434,7 @@ aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n, const aeb_hist
  *   host_stats  host aeb_stats written on success
  *   host_out    host columns for per-sample outputs, or NULL / NULL members
  * Above 2^19 samples the upload is cut into chunks of growing length (2^18
- * samples first, then six times the previous one), each rolled out as soon as
+ * samples first, then twice the previous one), each rolled out as soon as
  * it has arrived, on internal streams ordered after the work already queued
  * on `stream`; results are the same bits as one aeb_rollout + aeb_reduce of
  * all n samples (sample i keeps row i for its perception readings).

@@ -234,12 +234,14 @@ aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &
 // behind the arithmetic, and two compute streams let a chunk's launch start
 // while the previous one drains its last rollouts.  The first chunk is small,
 // so the arithmetic starts after a short upload; each later one is kEvalGrow
-// times the one before (an upload moves 80 B per sample, far faster than a
-// rollout of the sample, so a chunk's copy ends well before the previous
-// chunk's arithmetic), which keeps the launches, and their tails, few.
-constexpr int kEvalMaxChunks = 8;
+// times the one before.  A chunk's copy must end before the previous chunk's
+// rollouts do: an upload moves 80 B per sample (~1.3 ns per sample at the
+// pinned-host copy rate measured on GB300) against ~2.7 ns per sample of
+// FP32 rollout, so a chunk may be at most about twice the one before (six
+// times left the GPU waiting for the last chunk's copy).
+constexpr int kEvalMaxChunks = 12;
 constexpr uint64_t kEvalFirstChunk = uint64_t(1) << 18;
-constexpr uint64_t kEvalGrow = 6;
+constexpr uint64_t kEvalGrow = 2;
 struct EvalBuffers {
     void *base = nullptr;
     uint64_t cap = 0;  // samples

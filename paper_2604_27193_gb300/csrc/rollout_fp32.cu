@@ -508,8 +508,14 @@ struct Lane32 {
 #pragma unroll
             for (int j = 0; j < AEB_FP32_WINDOW; ++j) step_unchecked();
         } else {
+            // rolled (code size), two steps per trip, then the odd step
+            int j = 0;
 #pragma unroll 1
-            for (int j = 0; j < len; ++j) step_unchecked();
+            for (; j + 2 <= len; j += 2) {
+                step_unchecked();
+                step_unchecked();
+            }
+            if (j < len) step_unchecked();
         }
         normalize();
         bool hit = vh <= 0.0f;

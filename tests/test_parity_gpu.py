@@ -275,7 +275,7 @@ def test_evaluate_host_path(aeb, oracle_mod):
 @pytest.mark.parametrize("n", [2_500_003, 10_000_000])
 def test_evaluate_chunked_upload(aeb, n):
     """aeb_evaluate above 2^19 samples uploads and rolls out in chunks of
-    growing length on internal streams (2.5e6: three chunks, the last shorter
+    growing length on internal streams (2.5e6: four chunks, the last shorter
     than the one before; 1e7: the benchmark's end-to-end call); its outputs and
     statistics are byte-identical to one device-resident rollout and reduction
     of the same parameters."""
