@@ -233,7 +233,7 @@ enum {
 template <bool TTC>
 __host__ __device__ constexpr int cold_fields() { return TTC ? L_NW_TTC : L_NW_BASE; }
 
-template <int LEAD, bool TTC>
+template <int LEAD, bool TTC, bool PERC>
 struct Lane32 {
     float vh, vl, gh, gl, e;      // state: scaled speed w = s v, scaled gap G = sigma (d0 - x),
                                   // actuator deviation a - u
@@ -578,7 +578,10 @@ struct Lane32 {
     // first L - 1 steps after this one cannot trigger while (L - 1) times that
     // bound stays below the margin.  With a moving lead the margin is
     // (g + noise) - thr (v - v_L).
-    __device__ __forceinline__ int ttc_check(const ModelF32 &F, int32_t n_last)
+    // The trigger margin (g + noise) - thr v at the current state, scaled by
+    // sigma, with the exact rounding error of thr * vh; a moving lead adds its
+    // travel to the gap and takes its speed off the closing speed.
+    __device__ __forceinline__ float ttc_margin(const ModelF32 &F) const
     {
         const float thr_h = cf(L_THRH);
         const float p = thr_h * vh;
@@ -586,36 +589,58 @@ struct Lane32 {
         const float hi = gh - p;
         const float lo = (gl + cf(L_NZ)) - (pe + fmaf(thr_h, vl, cf(L_THRL) * vh));
         float m = hi + lo;
-        // moving lead: the gap grows by the lead's travel, the closing speed
-        // falls by its speed
         if (LEAD == kLeadMoving)
             m = m + fmaf(thr_h, lead_speed(F, n, cf(L_S)), lead_gap(F, n, cf(L_SIGMA)));
-        // per-step perception: the reading of step n + L (its noise, in the
-        // margin's units; no test if it is missing); uniforms from the top 24
-        // bits of the Philox words
-        bool reading = true;
-        float pn = 0.0f;
-        if (F.perc) {
-            const uint64_t krow = (uint64_t)(uint32_t)ci(L_KIDXLO) |
-                                  ((uint64_t)(uint32_t)ci(L_KIDXHI) << 32);
-            uint64_t c[4] = {krow, (uint64_t)((long long)n + F.plat), 0, 0};
-            philox_block(c, F.pseed, kPercKey1);
-            const float s24 = 5.9604644775390625e-8f;  // 2^-24
-            const float u1 = (float)(uint32_t)(c[0] >> 40) * s24;
-            const float u2 = (float)(uint32_t)(c[1] >> 40) * s24;
-            const float u3 = (float)(uint32_t)(c[2] >> 40) * s24;
-            const float u4 = (float)(uint32_t)(c[3] >> 40) * s24;
-            reading = !(u4 < F.pdrop);
-            pn = cf(L_SIGMA) * (F.psig * (2.0f * (((u1 + u2) + u3) - 1.5f)));
-        }
-        if (reading && m + pn <= 0.0f) {
-            trig = true;
-            const long long nb = ((long long)n + F.plat) + ci(L_NDELAY);
-            const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
-            set_ci(L_NB, n_b);
-            ev = (n_b < n_last) ? n_b : n_last;
-            return AEB_FP32_WINDOW;
-        }
+        return m;
+    }
+
+    // The noise of the reading of step k (taken at step k + L) in the margin's
+    // units of a lane with gap scale sig, or +inf if the reading is missing;
+    // uniforms from the top 24 bits of the Philox words.
+    static __device__ __forceinline__ float reading(const ModelF32 &F, uint64_t krow, int32_t k,
+                                                    float sig)
+    {
+        uint64_t c[4] = {krow, (uint64_t)((long long)k + F.plat), 0, 0};
+        philox_block(c, F.pseed, kPercKey1);
+        const float s24 = 5.9604644775390625e-8f;  // 2^-24
+        const float u1 = (float)(uint32_t)(c[0] >> 40) * s24;
+        const float u2 = (float)(uint32_t)(c[1] >> 40) * s24;
+        const float u3 = (float)(uint32_t)(c[2] >> 40) * s24;
+        const float u4 = (float)(uint32_t)(c[3] >> 40) * s24;
+        if (u4 < F.pdrop) return finf();
+        return sig * (F.psig * (2.0f * (((u1 + u2) + u3) - 1.5f)));
+    }
+
+    __device__ __forceinline__ uint64_t krow() const
+    {
+        return (uint64_t)(uint32_t)ci(L_KIDXLO) | ((uint64_t)(uint32_t)ci(L_KIDXHI) << 32);
+    }
+
+    // The trigger fires at step k (its onset step n_b = k + L + n_delay).
+    __device__ __forceinline__ void fire(const ModelF32 &F, int32_t k, int32_t n_last)
+    {
+        trig = true;
+        const long long nb = ((long long)k + F.plat) + ci(L_NDELAY);
+        const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
+        set_ci(L_NB, n_b);
+        ev = (n_b < n_last) ? n_b : n_last;
+    }
+
+    // How many steps (1 .. kTtcSpan; whole windows from K up) may run before
+    // the next trigger test, after the test of this step did not fire; 0 if
+    // with per-step perception even this step's test cannot be ruled out by
+    // the worst-case noise (the lane is in its noise band).
+    // Before the trigger the car coasts, the stage accelerations are
+    // q = w^2 + C >= C, so over the span the scaled speed stays below
+    // W = w + kTtcSpan s dt max(0, -C)
+    // and the margin falls by at most 6 W + thr' s dt max(0, -C) per step
+    // (the gap by the stage-speed sum, the speed term by the speed gain); the
+    // first L - 1 steps after this one cannot trigger while (L - 1) times that
+    // bound stays below the margin.  With a moving lead the margin is
+    // (g + noise) - thr (v - v_L).
+    __device__ __forceinline__ int ttc_bound(const ModelF32 &F, float m) const
+    {
+        const float thr_h = cf(L_THRH);
         const float sdt = -ndts, acc = fmaxf(0.0f, -C);
         const float W = fmaf((float)kTtcSpan * sdt, acc, vh + vl);  // speed bound over the span
         // (a braking lead's speed term falls by thr' s dt b_L per step more;
@@ -623,13 +648,85 @@ struct Lane32 {
         const float d = fmaf(6.0f, W, thr_h * sdt * (acc + F.lb)) * 1.001f;
         // a reading's noise is at most 3 perc_sigma: only a margin beyond that
         // rules a trigger out whatever the readings of the skipped steps
-        const float mw = F.perc ? fmaf(-3.0f * F.psig, cf(L_SIGMA), m) : m;
+        const float mw = PERC ? fmaf(-3.0f * F.psig, cf(L_SIGMA), m) : m;
         const float r = __fdividef(mw, d) * 0.999f;
-        if (!(r > 0.0f)) return 1;
+        if (!(r > 0.0f)) return PERC ? 0 : 1;
         const int t = r >= (float)(kTtcSpan - 1) ? kTtcSpan : 1 + (int)r;
         // a span of whole windows (testing earlier is always safe), so that
         // far from the trigger the next test falls on a window boundary
         return t >= AEB_FP32_WINDOW ? t - t % AEB_FP32_WINDOW : t;
+    }
+
+    // TTC trigger test of this step (while not yet triggered): (g + noise) -
+    // thr v <= 0 (with per-step perception: this step's reading, none if it is
+    // missing); braking starts n_delay steps later.  Returns how many steps
+    // (1 .. kTtcSpan) may run before the next test (K once triggered).
+    __device__ __forceinline__ int ttc_check(const ModelF32 &F, int32_t n_last)
+    {
+        const float m = ttc_margin(F);
+        const float pn = PERC ? reading(F, krow(), n, cf(L_SIGMA)) : 0.0f;
+        if (m + pn <= 0.0f) {  // a missing reading (+inf) never fires
+            fire(F, n, n_last);
+            return AEB_FP32_WINDOW;
+        }
+        const int t = ttc_bound(F, m);
+        return t > 0 ? t : 1;
+    }
+
+    // Per-step perception, a lane in its noise band with its readings `rd`
+    // for steps n .. n + K - 1 (other lanes: rd == nullptr): up to `len` steps
+    // with the trigger tested before each (the margin formed as in
+    // ttc_margin, from the pair words of the window); a trigger at step n + j
+    // cuts the window at its onset step (or the last step).  Returns true if
+    // the rollout ended inside (state back at the window's start, as
+    // step_window); `trel` is the trigger's step in the window (-1: none), and
+    // the trigger stays recorded (the flush drops it if the rollout ended
+    // before that step).
+    __device__ __forceinline__ bool step_window_band(const ModelF32 &F, int &len, const float *rd,
+                                                     int &trel, int32_t n_last)
+    {
+        const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
+        trel = -1;
+        float thr_h = 0.0f, pe = 0.0f, hi = 0.0f, c1 = 0.0f, nz = 0.0f, sl = 0.0f, sg = 0.0f;
+        if (rd) {
+            thr_h = cf(L_THRH);
+            const float p = thr_h * vh;
+            pe = fmaf(thr_h, vh, -p);
+            hi = gh - p;
+            c1 = cf(L_THRL) * vh;
+            nz = cf(L_NZ);
+            sl = cf(L_S);
+            sg = cf(L_SIGMA);
+        }
+#pragma unroll 1
+        for (int j = 0; j < len; ++j) {
+            if (rd && trel < 0) {
+                float m = hi + ((gl + nz) - (pe + fmaf(thr_h, vl, c1)));
+                if (LEAD == kLeadMoving)
+                    m = m + fmaf(thr_h, lead_speed(F, n + j, sl), lead_gap(F, n + j, sg));
+                if (m + rd[j] <= 0.0f) {
+                    trel = j;
+                    fire(F, n + j, n_last);
+                    if (ev - n < len) len = ev - n;  // stop at the onset step
+                    if (j >= len) break;
+                }
+            }
+            step_unchecked();
+        }
+        normalize();
+        bool hit = vh <= 0.0f;
+        if (LEAD == kLeadStationary) hit = hit || gh <= 0.0f;
+        if (LEAD == kLeadMoving) hit = hit || gh + lead_gap(F, n + len, cf(L_SIGMA)) <= 0.0f;
+        if (hit) {
+            vh = vh0;
+            vl = vl0;
+            gh = gh0;
+            gl = gl0;
+            e = e0;
+            return true;
+        }
+        n += len;
+        return false;
     }
 
     // Load sample `slot` of the warp's tile (parameter row pi, output row i);
@@ -721,21 +818,25 @@ enum {
 enum { B_G1H = B_A1, B_G1L = B_A2, B_W1H = B_A3, B_W1L = B_A4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
-template <bool TTC>
+// Per-step perception: the readings of up to kBandSlots lanes near their
+// trigger, for the next K steps each, in the margin's units (+inf: missing).
+constexpr int kBandSlots = 4;
+template <bool TTC, bool PERC>
 __host__ __device__ constexpr int warp_words(int T)
 {
-    return (rec_floats<TTC>() + R_NI) * T + kBatchWords + cold_fields<TTC>() * 32;
+    return (rec_floats<TTC>() + R_NI) * T + kBatchWords + cold_fields<TTC>() * 32 +
+           (PERC ? kBandSlots * AEB_FP32_WINDOW : 0);
 }
-template <bool TTC>
+template <bool TTC, bool PERC>
 __host__ __device__ constexpr size_t smem_per_block(int T)
 {
-    return sizeof(float) * warp_words<TTC>(T) * kWarps;
+    return sizeof(float) * warp_words<TTC, PERC>(T) * kWarps;
 }
 
 // For the warp's queued records, all 32 lanes at once: replay the windows that
 // contained an end one checked step at a time, then the binary64 refinement
 // of the last step (Sec. V-D termination; the refinement of the last step).
-template <int LEAD, bool TTC>
+template <int LEAD, bool TTC, bool PERC>
 __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F,
                                             const ParamsDev &P, const OutDev &O,
                                             const float *bf, const int *bi, int count)
@@ -747,13 +848,14 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
                            ((uint64_t)(uint32_t)bi[B_IDXHI * 32 + j] << 32);
         const uint64_t pi = (uint64_t)(uint32_t)bi[B_PIDXLO * 32 + j] |
                             ((uint64_t)(uint32_t)bi[B_PIDXHI * 32 + j] << 32);
-        const int len = bi[B_LEN * 32 + j];
-        const int32_t on = bi[B_ONSET * 32 + j];
+        const int len = bi[B_LEN * 32 + j] & 0xff;
+        const int trel = (bi[B_LEN * 32 + j] >> 8) - 1;  // trigger step in the window (-1: none)
+        int32_t on = bi[B_ONSET * 32 + j];
         int status;
         int32_t n1;
         float g0h, g0l, w0h, w0l, g1h, g1l, w1h, w1l;
         if (len > 0) {
-            Lane32<LEAD, TTC> R;
+            Lane32<LEAD, TTC, PERC> R;
             R.vh = bf[B_VH * 32 + j];
             R.vl = bf[B_VL * 32 + j];
             R.gh = bf[B_GH * 32 + j];
@@ -769,6 +871,7 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             R.nmP = bf[B_NMP * 32 + j];
             R.C = bf[B_C * 32 + j];
             R.n = bi[B_N * 32 + j];
+            const int32_t nstart = R.n;
             // ends within len steps: the window's last state is terminal
             float vl1, gl1;
             const float sig = bf[B_SIGMA * 32 + j];
@@ -784,6 +887,9 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
             w1l = vl1;
             n1 = R.n + 1;
             status = R.hits_lead(F, gl1, sig) ? AEB_CONTACT : AEB_STOP;
+            // a trigger tested inside the window after the rollout's last step
+            // never happened
+            if (trel >= 0 && nstart + trel > n1 - 1) on = -1;
         } else {
             g0h = bf[B_GH * 32 + j];
             g0l = bf[B_GL * 32 + j];
@@ -839,24 +945,25 @@ __device__ __forceinline__ void flush_batch(const ModelDev &M, const ModelF32 &F
 // One warp walks tiles of kTile samples claimed from a global counter; see the
 // file comment.  No wait on other warps or on the host: the loop ends when the
 // tiles are used up and no lane holds a rollout.
-template <int LEAD, bool TTC>
-__global__ void __launch_bounds__(kThreads, AEB_FP32_MIN_BLOCKS)
+template <int LEAD, bool TTC, bool PERC>
+__global__ void __launch_bounds__(kThreads, PERC ? 5 : AEB_FP32_MIN_BLOCKS)
 k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
 {
     extern __shared__ float smem[];
     const unsigned lane = threadIdx.x & 31u;
     const int T = (int)W.tile;
-    float *tf = smem + (threadIdx.x >> 5) * warp_words<TTC>(T);
+    float *tf = smem + (threadIdx.x >> 5) * warp_words<TTC, PERC>(T);
     int *ti = reinterpret_cast<int *>(tf + rec_floats<TTC>() * T);
     float *bf = tf + (rec_floats<TTC>() + R_NI) * T;
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
     float *coldw = bf + kBatchWords;
+    float *rdg = coldw + cold_fields<TTC>() * 32;  // band readings (per-step perception)
     const int32_t n_last = M.n_max - 1;
 
     Tile tile{};
     int cursor = 0, bcount = 0;
     bool dry = false;
-    Lane32<LEAD, TTC> L;
+    Lane32<LEAD, TTC, PERC> L;
     L.cold = coldw + lane;
     bool active = false;
     unsigned need = kFull;
@@ -893,7 +1000,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 need = (need & ~taken) | __ballot_sync(kFull, ended);
             }
             if (!__any_sync(kFull, active)) {
-                flush_batch<LEAD, TTC>(M, F, P, O, bf, bi, bcount);
+                flush_batch<LEAD, TTC, PERC>(M, F, P, O, bf, bi, bcount);
                 return;
             }
         }
@@ -902,11 +1009,56 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         bool ended = false;
         float vl1, gl1;  // end-of-step low words of a slow step that ended
         int tlen = AEB_FP32_WINDOW;  // steps before the next TTC test
+        int slot = -1, trel = -1;    // per-step perception: readings slot, trigger step
+        bool wait = false;           // per-step perception: a band lane waiting for a slot
         if (TTC && active && !L.trig) {
             tlen = L.ci(L_NCHK) - L.n;  // steps the last test still covers
             if (tlen <= 0) {
-                tlen = L.ttc_check(F, n_last);
-                if (!L.trig) L.set_ci(L_NCHK, L.n + tlen);
+                if (PERC) {  // no reading needed unless the worst-case noise can trigger
+                    tlen = L.ttc_bound(F, L.ttc_margin(F));
+                    if (tlen > 0) L.set_ci(L_NCHK, L.n + tlen);
+                } else {
+                    tlen = L.ttc_check(F, n_last);
+                    if (!L.trig) L.set_ci(L_NCHK, L.n + tlen);
+                }
+            }
+        }
+        if (PERC) {
+            // Lanes in their noise band (every step needs its reading): up to
+            // kBandSlots of them get the readings of their next K steps,
+            // generated at full warp width (one Philox block per lane), and
+            // test the trigger inside their window; the others wait for a
+            // later pass (so that a sample's windows, and its arithmetic, never
+            // depend on the lanes it shares a warp with), and a lane at its
+            // last step (no window) tests that step alone.
+            const bool band = active && !L.trig && tlen <= 0;
+            const unsigned bm = __ballot_sync(kFull, band && !L.at_slow(n_last));
+            if (bm) {
+                const int rank = __popc(bm & lanemask_lt());
+                if (((bm >> lane) & 1u) && rank < kBandSlots) slot = rank;
+                const int nb = __popc(bm) < kBandSlots ? __popc(bm) : kBandSlots;
+                const int klo = L.ci(L_KIDXLO), khi = L.ci(L_KIDXHI);
+                const float sgl = L.cf(L_SIGMA);
+                unsigned rest = bm;
+                for (int sb = 0; sb < nb; ++sb) {
+                    const int src = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const uint64_t kr = (uint64_t)(uint32_t)__shfl_sync(kFull, klo, src) |
+                                        ((uint64_t)(uint32_t)__shfl_sync(kFull, khi, src) << 32);
+                    const int32_t ns = __shfl_sync(kFull, L.n, src);
+                    const float sig = __shfl_sync(kFull, sgl, src);
+                    const float r = L.reading(F, kr, ns + (int32_t)lane, sig);
+                    if ((int)lane < AEB_FP32_WINDOW) rdg[sb * AEB_FP32_WINDOW + lane] = r;
+                }
+                __syncwarp();
+            }
+            if (band && slot < 0) {
+                if (L.at_slow(n_last)) {
+                    tlen = L.ttc_check(F, n_last);
+                    if (!L.trig) L.set_ci(L_NCHK, L.n + tlen);
+                } else {
+                    wait = true;
+                }
             }
         }
         // Most passes: every active lane can run a full window (no event in
@@ -920,12 +1072,20 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 if (onset) L.onset_event(F, n_last);
             }
             // a lane already at a slow step runs no window in this pass
-            if (active) len = L.at_slow(n_last) ? 0 : L.window_len(tlen);
-            full = __all_sync(kFull, len == AEB_FP32_WINDOW);
+            if (active)
+                len = (wait || L.at_slow(n_last)) ? 0
+                                                  : L.window_len(slot >= 0 ? AEB_FP32_WINDOW : tlen);
+            // (a lane with readings tests its trigger in the band window, never
+            // in the unrolled full one)
+            full = __all_sync(kFull, len == AEB_FP32_WINDOW && slot < 0);
         }
         bool replay = false;
         if (full) {
             if (active) replay = L.template step_window<true>(F, len);
+        } else if (PERC && __any_sync(kFull, slot >= 0)) {
+            if (active && len > 0)
+                replay = L.step_window_band(F, len, slot >= 0 ? rdg + slot * AEB_FP32_WINDOW : nullptr,
+                                            trel, n_last);
         } else {
             if (active && len > 0) replay = L.template step_window<false>(F, len);
         }
@@ -943,7 +1103,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         if (endm) {
             const int cnt = __popc(endm);
             if (bcount + cnt > 32) {
-                flush_batch<LEAD, TTC>(M, F, P, O, bf, bi, bcount);
+                flush_batch<LEAD, TTC, PERC>(M, F, P, O, bf, bi, bcount);
                 bcount = 0;
             }
             if (ended) {
@@ -970,7 +1130,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     bf[B_NMP * 32 + j] = L.nmP;
                     bf[B_C * 32 + j] = L.C;
                     bi[B_N * 32 + j] = L.n;
-                    bi[B_LEN * 32 + j] = len;
+                    bi[B_LEN * 32 + j] = len | ((trel + 1) << 8);  // + a trigger in the window
                 } else {
                     bf[B_G1H * 32 + j] = L.gh;
                     bf[B_G1L * 32 + j] = gl1;
@@ -1013,14 +1173,14 @@ ModelF32 to_f32(const ModelDev &m)
     return f;
 }
 
-template <int LEAD, bool TTC>
+template <int LEAD, bool TTC, bool PERC>
 cudaError_t launch_t(const ModelDev &m, const ParamsDev &p, const OutDev &o, const WorkDev &w,
                      const LaunchCfg &cfg, cudaStream_t s)
 {
-    auto kern = k_rollout_fp32<LEAD, TTC>;
+    auto kern = k_rollout_fp32<LEAD, TTC, PERC>;
     const int T = w.tiles ? (int)w.tile : (cfg.tile > 0 ? cfg.tile : kTileDefault);
     if (T < 32 || T > kTileMax || T % 32) return cudaErrorInvalidValue;
-    const size_t smem = smem_per_block<TTC>(T);
+    const size_t smem = smem_per_block<TTC, PERC>(T);
     int dev = 0, sms = 0, per_sm = cfg.blocks_per_sm;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1052,11 +1212,19 @@ cudaError_t launch_rollout_fp32(const ModelDev &m, const ParamsDev &p, const Out
                                 const WorkDev &w, const LaunchCfg &cfg, cudaStream_t s)
 {
     const bool ttc = m.trigger == AEB_TRIGGER_TTC;
-    if (m.lead_moving) return ttc ? launch_t<kLeadMoving, true>(m, p, o, w, cfg, s)
-                                  : launch_t<kLeadMoving, false>(m, p, o, w, cfg, s);
-    if (m.lead) return ttc ? launch_t<kLeadStationary, true>(m, p, o, w, cfg, s)
-                           : launch_t<kLeadStationary, false>(m, p, o, w, cfg, s);
-    return ttc ? launch_t<kNoLead, true>(m, p, o, w, cfg, s) : launch_t<kNoLead, false>(m, p, o, w, cfg, s);
+    // per-step perception readings (TTC trigger only) have their own kernels
+    const bool perc = ttc && m.perc;
+    if (m.lead_moving)
+        return perc ? launch_t<kLeadMoving, true, true>(m, p, o, w, cfg, s)
+                    : ttc ? launch_t<kLeadMoving, true, false>(m, p, o, w, cfg, s)
+                          : launch_t<kLeadMoving, false, false>(m, p, o, w, cfg, s);
+    if (m.lead)
+        return perc ? launch_t<kLeadStationary, true, true>(m, p, o, w, cfg, s)
+                    : ttc ? launch_t<kLeadStationary, true, false>(m, p, o, w, cfg, s)
+                          : launch_t<kLeadStationary, false, false>(m, p, o, w, cfg, s);
+    return perc ? launch_t<kNoLead, true, true>(m, p, o, w, cfg, s)
+                : ttc ? launch_t<kNoLead, true, false>(m, p, o, w, cfg, s)
+                      : launch_t<kNoLead, false, false>(m, p, o, w, cfg, s);
 }
 
 }  // namespace aeb
