@@ -675,9 +675,10 @@ struct Lane32 {
 
     // Per-step perception, a lane in its noise band with its readings `rd`
     // for steps n .. n + K - 1 (other lanes: rd == nullptr): up to `len` steps
-    // with the trigger tested before each (the margin formed as in
-    // ttc_margin, from the pair words of the window); a trigger at step n + j
-    // cuts the window at its onset step (or the last step).  Returns true if
+    // with the trigger tested before each (the margin of ttc_margin with its
+    // window-constant part hk taken once: the high words stay fixed in a
+    // window); a trigger at step n + j cuts the window at its onset step (or
+    // the last step).  Returns true if
     // the rollout ended inside (state back at the window's start, as
     // step_window); `trel` is the trigger's step in the window (-1: none), and
     // the trigger stays recorded (the flush drops it if the rollout ended
@@ -698,10 +699,11 @@ struct Lane32 {
             sl = cf(L_S);
             sg = cf(L_SIGMA);
         }
+        const float hk = hi + (nz - pe);  // the margin's window-constant part
 #pragma unroll 1
         for (int j = 0; j < len; ++j) {
             if (rd && trel < 0) {
-                float m = hi + ((gl + nz) - (pe + fmaf(thr_h, vl, c1)));
+                float m = (gl + hk) - fmaf(thr_h, vl, c1);
                 if (LEAD == kLeadMoving)
                     m = m + fmaf(thr_h, lead_speed(F, n + j, sl), lead_gap(F, n + j, sg));
                 if (m + rd[j] <= 0.0f) {
