@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define AEB_ABI_VERSION 5
+#define AEB_ABI_VERSION 6
 #define AEB_NFIELDS 10   /* columns of a parameter set, see aeb_params       */
 #define AEB_NBINS 4096   /* bins of each fixed histogram in aeb_stats         */
 
@@ -100,10 +100,12 @@ typedef struct aeb_model {
     /* Per-step perception of the TTC trigger's readings (extension).  The
        reading used at step n is taken L steps later (L = smallest integer with
        L dt >= perc_latency) and describes step n; it is missing with
-       probability perc_drop, else carries the noise
+       probability perc_drop (u4 < perc_drop), else carries the noise
        perc_sigma * 2 ((u1 + u2) + u3 - 1.5) (zero mean, unit variance, within
-       +-3 perc_sigma), u_j = (w_j >> 11) 2^-53 from the Philox-4x64-10 block of
-       counter (parameter row, n + L, 0, 0) under key (perc_seed, 0x5045524345505431).
+       +-3 perc_sigma), u_j = h_j 2^-32, h_j the high 32-bit halves (k = n + L
+       even) or the low halves (k odd) of the four words of the Philox-4x64-10
+       block of counter (parameter row, floor(k / 2), 0, 0) under key
+       (perc_seed, 0x5045524345505431).
        A trigger at step n starts braking at n + L + n_delay.  All zero: the
        plain trigger.  perc_sigma, perc_latency finite and >= 0, perc_drop in
        [0, 1], else AEB_EINVAL.                                                 */

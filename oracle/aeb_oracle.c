@@ -436,23 +436,30 @@ static double lead_speed(const om_model *m, double t)
  * Per-step perception (extension; Sec. VIII names noise, latency and dropout
  * of the perception chain as future work), TTC trigger only.  The reading
  * taken at step k = n + L describes the state of step n (L = smallest integer
- * with L dt >= perc_latency).  Its words are Philox-4x64-10 of counter
- * (sample row, k, 0, 0) under key (perc_seed, "PERCEPT1"); with the uniforms
- * u_j = (w_j >> 11) 2^-53, the reading is missing if u_4 < perc_drop, else its
- * noise is perc_sigma * 2 ((u_1 + u_2) + u_3 - 1.5): zero mean, unit variance
- * (Irwin-Hall of three uniforms, bounded by +-3 perc_sigma, close to normal),
- * so no transcendental function enters the trigger decision.
+ * with L dt >= perc_latency).  Two consecutive readings share one
+ * Philox-4x64-10 block, of counter (sample row, floor(k / 2), 0, 0) under key
+ * (perc_seed, "PERCEPT1"): reading k takes the high 32-bit halves h_j of the
+ * block's four words if k is even, the low halves if k is odd.  With the
+ * uniforms u_j = h_j 2^-32, the reading is missing if u_4 < perc_drop, else
+ * its noise is perc_sigma * 2 ((u_1 + u_2) + u_3 - 1.5): zero mean (to
+ * 2^-32 perc_sigma), unit variance (Irwin-Hall of three uniforms, bounded by
+ * +-3 perc_sigma, close to normal), so no transcendental function enters the
+ * trigger decision.  (The paper fixes no generator; sharing a block between
+ * two readings halves the work of drawing them.)
  */
 static const uint64_t PERC_KEY1 = 0x5045524345505431ULL; /* "PERCEPT1" */
 
 /* Returns 0 if the reading of step k is missing, else 1 and its noise. */
 static int perception(const om_model *m, uint64_t row, int64_t k, double *noise)
 {
-    const double two_m53 = 1.0 / 9007199254740992.0; /* 2^-53 */
-    uint64_t ctr[4] = {row, (uint64_t)k, 0, 0}, key[2] = {m->perc_seed, PERC_KEY1}, w[4];
+    const double two_m32 = 1.0 / 4294967296.0; /* 2^-32 */
+    uint64_t ctr[4] = {row, (uint64_t)k >> 1, 0, 0}, key[2] = {m->perc_seed, PERC_KEY1}, w[4];
     om_philox4x64_10(ctr, key, w);
-    double u1 = (double)(w[0] >> 11) * two_m53, u2 = (double)(w[1] >> 11) * two_m53;
-    double u3 = (double)(w[2] >> 11) * two_m53, u4 = (double)(w[3] >> 11) * two_m53;
+    const int sh = (k & 1) ? 0 : 32; /* even k: high halves; odd k: low halves */
+    double u1 = (double)((w[0] >> sh) & 0xffffffffULL) * two_m32;
+    double u2 = (double)((w[1] >> sh) & 0xffffffffULL) * two_m32;
+    double u3 = (double)((w[2] >> sh) & 0xffffffffULL) * two_m32;
+    double u4 = (double)((w[3] >> sh) & 0xffffffffULL) * two_m32;
     if (u4 < m->perc_drop) return 0;
     *noise = m->perc_sigma * (2.0 * (((u1 + u2) + u3) - 1.5));
     return 1;

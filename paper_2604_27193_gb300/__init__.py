@@ -24,7 +24,7 @@ OUTPUTS = ("status", "x_raw", "x_ref", "v_imp", "t_end", "n_steps", "n_onset")
 OUT_DTYPES = {"status": np.uint8, "x_raw": np.float64, "x_ref": np.float64,
               "v_imp": np.float64, "t_end": np.float64, "n_steps": np.int32,
               "n_onset": np.int32}
-ABI_VERSION = 5  # AEB_ABI_VERSION of include/aeb.h
+ABI_VERSION = 6  # AEB_ABI_VERSION of include/aeb.h
 NBINS = 4096
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ECANCELLED, EDEVICE = range(8)

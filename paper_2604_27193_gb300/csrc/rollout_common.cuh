@@ -109,8 +109,8 @@ struct WarpQueue {
 
 // Philox-4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011): the block of counter
 // c under key (k0, k1), in place.  Used for the per-step perception readings
-// of the TTC trigger, counter (parameter row, step, 0, 0), key (seed,
-// kPercKey1).
+// of the TTC trigger, two readings per block: counter (parameter row,
+// floor(k / 2), 0, 0), key (seed, kPercKey1) (see perc_halves).
 constexpr uint64_t kPercKey1 = 0x5045524345505431ull;  // "PERCEPT1"
 __device__ __forceinline__ void philox_block(uint64_t c[4], uint64_t k0, uint64_t k1)
 {
@@ -128,6 +128,19 @@ __device__ __forceinline__ void philox_block(uint64_t c[4], uint64_t k0, uint64_
         k0 += kW0;
         k1 += kW1;
     }
+}
+
+// The four 32-bit words h_j of reading k (taken at step k) of parameter row
+// `row`: the high halves of the block's words for even k, the low halves for
+// odd k.  Uniforms u_j = h_j 2^-32; the reading is missing if u_4 is below
+// the dropout probability.
+__device__ __forceinline__ void perc_halves(uint64_t row, uint64_t k, uint64_t seed, uint32_t h[4])
+{
+    uint64_t c[4] = {row, k >> 1, 0, 0};
+    philox_block(c, seed, kPercKey1);
+    const int sh = (k & 1) ? 0 : 32;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = (uint32_t)(c[j] >> sh);
 }
 
 // A sample is invalid if any field is not finite, mass <= 0, or tau, mu, C_d

@@ -48,7 +48,7 @@
 // lane queues its terminal state in the warp's shared slab, and the warp refines
 // 32 queued rollouts at once.
 //
-// Steps run in windows of up to K = 16 with no test in between.  A lane's
+// Steps run in windows of up to K = 32 with no test in between.  A lane's
 // window ends before its next event (brake onset, the last step before the
 // horizon, a step that crosses a breakpoint of r(D), and before a TTC trigger
 // the next step at which the trigger could fire); lanes of a warp with
@@ -57,6 +57,7 @@
 // steps (new command, new piece); only the breakpoint-crossing step and the
 // last step take a slow path that evaluates the full minimum per stage.
 #include <climits>
+#include <cmath>
 
 #include "rollout_common.cuh"
 
@@ -101,8 +102,10 @@ struct ModelF32 {
     // stop position (binary32 copies of the model's values)
     float dt, lv0, lb, lhb, lts, lxs;
     // per-step perception of the TTC trigger (see the model): noise scale,
-    // dropout probability, latency in steps, stream key, any of them set
-    float psig, pdrop;
+    // dropout threshold on a reading's h_4 (ceil(perc_drop 2^32): h_4 below it
+    // is exactly u_4 < perc_drop), latency in steps, stream key, any of them set
+    float psig;
+    uint64_t pdrop_h;
     uint64_t pseed;
     int plat, perc;
 };
@@ -594,21 +597,43 @@ struct Lane32 {
         return m;
     }
 
-    // The noise of the reading of step k (taken at step k + L) in the margin's
-    // units of a lane with gap scale sig, or +inf if the reading is missing;
-    // uniforms from the top 24 bits of the Philox words.
+    // The noise of a reading with words h (perc_halves) in the margin's units
+    // of a lane with gap scale sig, or +inf if the reading is missing: the
+    // dropout decision is the exact integer form of u_4 < perc_drop, the
+    // noise takes the top 24 bits of h_1 .. h_3.
+    static __device__ __forceinline__ float reading_of(const ModelF32 &F, const uint32_t h[4],
+                                                       float sig)
+    {
+        if ((uint64_t)h[3] < F.pdrop_h) return finf();
+        const float s24 = 5.9604644775390625e-8f;  // 2^-24
+        const float u1 = (float)(h[0] >> 8) * s24;
+        const float u2 = (float)(h[1] >> 8) * s24;
+        const float u3 = (float)(h[2] >> 8) * s24;
+        return sig * (F.psig * (2.0f * (((u1 + u2) + u3) - 1.5f)));
+    }
+
+    // The reading of step k (taken at step k + L).
     static __device__ __forceinline__ float reading(const ModelF32 &F, uint64_t krow, int32_t k,
                                                     float sig)
     {
-        uint64_t c[4] = {krow, (uint64_t)((long long)k + F.plat), 0, 0};
+        uint32_t h[4];
+        perc_halves(krow, (uint64_t)((long long)k + F.plat), F.pseed, h);
+        return reading_of(F, h, sig);
+    }
+
+    // Readings 2b and 2b + 1 (one Philox block): ra, rb.
+    static __device__ __forceinline__ void reading_pair(const ModelF32 &F, uint64_t krow,
+                                                        uint64_t b, float sig, float &ra, float &rb)
+    {
+        uint64_t c[4] = {krow, b, 0, 0};
         philox_block(c, F.pseed, kPercKey1);
-        const float s24 = 5.9604644775390625e-8f;  // 2^-24
-        const float u1 = (float)(uint32_t)(c[0] >> 40) * s24;
-        const float u2 = (float)(uint32_t)(c[1] >> 40) * s24;
-        const float u3 = (float)(uint32_t)(c[2] >> 40) * s24;
-        const float u4 = (float)(uint32_t)(c[3] >> 40) * s24;
-        if (u4 < F.pdrop) return finf();
-        return sig * (F.psig * (2.0f * (((u1 + u2) + u3) - 1.5f)));
+        uint32_t h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = (uint32_t)(c[j] >> 32);
+        ra = reading_of(F, h, sig);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = (uint32_t)c[j];
+        rb = reading_of(F, h, sig);
     }
 
     __device__ __forceinline__ uint64_t krow() const
@@ -616,10 +641,12 @@ struct Lane32 {
         return (uint64_t)(uint32_t)ci(L_KIDXLO) | ((uint64_t)(uint32_t)ci(L_KIDXHI) << 32);
     }
 
-    // The trigger fires at step k (its onset step n_b = k + L + n_delay).
+    // The trigger fires at step k (its onset step n_b = k + L + n_delay); the
+    // step stays in the test-step field, which is not read once triggered.
     __device__ __forceinline__ void fire(const ModelF32 &F, int32_t k, int32_t n_last)
     {
         trig = true;
+        if (PERC) set_ci(L_NCHK, k);
         const long long nb = ((long long)k + F.plat) + ci(L_NDELAY);
         const int32_t n_b = nb > INT_MAX ? INT_MAX : (int32_t)nb;
         set_ci(L_NB, n_b);
@@ -673,45 +700,37 @@ struct Lane32 {
         return t > 0 ? t : 1;
     }
 
-    // Per-step perception, a lane in its noise band with its readings `rd`
-    // for steps n .. n + K - 1 (other lanes: rd == nullptr): up to `len` steps
-    // with the trigger tested before each (the margin of ttc_margin with its
-    // window-constant part hk taken once: the high words stay fixed in a
-    // window); a trigger at step n + j cuts the window at its onset step (or
-    // the last step).  Returns true if
-    // the rollout ended inside (state back at the window's start, as
-    // step_window); `trel` is the trigger's step in the window (-1: none), and
-    // the trigger stays recorded (the flush drops it if the rollout ended
-    // before that step).
-    __device__ __forceinline__ bool step_window_band(const ModelF32 &F, int &len, const float *rd,
-                                                     int &trel, int32_t n_last)
+    // Per-step perception, the windows of a pass with lanes in their noise
+    // band: `len` steps as step_window<false>; a band lane (state slot `st`)
+    // also keeps the window's start (vh, gh, e at st[2K .. 2K + 2]) and, before
+    // each step j, its low words gl (st[j]) and vl (st[K + j]), on which the
+    // warp tests its trigger after the window (band_test).
+    __device__ __forceinline__ bool step_window_st(const ModelF32 &F, int len, float *st)
     {
         const float vh0 = vh, vl0 = vl, gh0 = gh, gl0 = gl, e0 = e;
-        trel = -1;
-        float thr_h = 0.0f, pe = 0.0f, hi = 0.0f, c1 = 0.0f, nz = 0.0f, sl = 0.0f, sg = 0.0f;
-        if (rd) {
-            thr_h = cf(L_THRH);
-            const float p = thr_h * vh;
-            pe = fmaf(thr_h, vh, -p);
-            hi = gh - p;
-            c1 = cf(L_THRL) * vh;
-            nz = cf(L_NZ);
-            sl = cf(L_S);
-            sg = cf(L_SIGMA);
+        if (st) {
+            st[2 * AEB_FP32_WINDOW] = vh;
+            st[2 * AEB_FP32_WINDOW + 1] = gh;
+            st[2 * AEB_FP32_WINDOW + 2] = e;
         }
-        const float hk = hi + (nz - pe);  // the margin's window-constant part
+        int j = 0;
 #pragma unroll 1
-        for (int j = 0; j < len; ++j) {
-            if (rd && trel < 0) {
-                float m = (gl + hk) - fmaf(thr_h, vl, c1);
-                if (LEAD == kLeadMoving)
-                    m = m + fmaf(thr_h, lead_speed(F, n + j, sl), lead_gap(F, n + j, sg));
-                if (m + rd[j] <= 0.0f) {
-                    trel = j;
-                    fire(F, n + j, n_last);
-                    if (ev - n < len) len = ev - n;  // stop at the onset step
-                    if (j >= len) break;
-                }
+        for (; j + 2 <= len; j += 2) {
+            if (st) {
+                st[j] = gl;
+                st[AEB_FP32_WINDOW + j] = vl;
+            }
+            step_unchecked();
+            if (st) {
+                st[j + 1] = gl;
+                st[AEB_FP32_WINDOW + j + 1] = vl;
+            }
+            step_unchecked();
+        }
+        if (j < len) {
+            if (st) {
+                st[j] = gl;
+                st[AEB_FP32_WINDOW + j] = vl;
             }
             step_unchecked();
         }
@@ -729,6 +748,31 @@ struct Lane32 {
         }
         n += len;
         return false;
+    }
+
+    // The trigger margin of ttc_margin at a step of a window whose start had
+    // the high words vh, gh, split into its window-constant part hk and the
+    // scaled-threshold parts thr_h, c1 (the high words stay fixed in a window):
+    // margin = (gl + hk) - fmaf(thr_h, vl, c1).
+    __device__ __forceinline__ void band_consts(float &thr_h, float &c1, float &hk) const
+    {
+        thr_h = cf(L_THRH);
+        const float p = thr_h * vh;
+        const float pe = fmaf(thr_h, vh, -p);
+        const float hi = gh - p;
+        c1 = cf(L_THRL) * vh;
+        hk = hi + (cf(L_NZ) - pe);
+    }
+
+    // Back to the start of the band window just run (its state slot st).
+    __device__ __forceinline__ void band_rewind(const float *st, int32_t n0)
+    {
+        vh = st[2 * AEB_FP32_WINDOW];
+        gh = st[2 * AEB_FP32_WINDOW + 1];
+        e = st[2 * AEB_FP32_WINDOW + 2];
+        gl = st[0];
+        vl = st[AEB_FP32_WINDOW];
+        n = n0;
     }
 
     // Load sample `slot` of the warp's tile (parameter row pi, output row i);
@@ -820,14 +864,21 @@ enum {
 enum { B_G1H = B_A1, B_G1L = B_A2, B_W1H = B_A3, B_W1L = B_A4 };
 enum { B_IDXLO, B_IDXHI, B_PIDXLO, B_PIDXHI, B_STATUS, B_N, B_LEN, B_ONSET, B_NI };
 constexpr int kBatchWords = (B_NF + B_NI) * 32;
-// Per-step perception: the readings of up to kBandSlots lanes near their
-// trigger, for the next K steps each, in the margin's units (+inf: missing).
-constexpr int kBandSlots = 4;
+// Per-step perception: readings of up to kBandSlots lanes near their trigger,
+// kBandCache steps each, in the margin's units (+inf: missing), and per slot
+// the tag of what it holds: the reading row (two words), the first step and
+// the count.
+constexpr int kBandSlots = 3;
+constexpr int kBandCache = 2 * AEB_FP32_WINDOW;
+enum { G_KLO, G_KHI, G_STEP, G_CNT, G_NI };
+// and per slot the band window's states (step_window_st): 2K low words, the
+// window's start, one word of padding (slots in different banks)
+constexpr int kBandState = 2 * AEB_FP32_WINDOW + 4;
 template <bool TTC, bool PERC>
 __host__ __device__ constexpr int warp_words(int T)
 {
     return (rec_floats<TTC>() + R_NI) * T + kBatchWords + cold_fields<TTC>() * 32 +
-           (PERC ? kBandSlots * AEB_FP32_WINDOW : 0);
+           (PERC ? kBandSlots * (kBandCache + G_NI + kBandState) : 0);
 }
 template <bool TTC, bool PERC>
 __host__ __device__ constexpr size_t smem_per_block(int T)
@@ -960,7 +1011,18 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
     float *coldw = bf + kBatchWords;
     float *rdg = coldw + cold_fields<TTC>() * 32;  // band readings (per-step perception)
+    int *btag = reinterpret_cast<int *>(rdg + kBandSlots * kBandCache);
+    float *sst = reinterpret_cast<float *>(btag + kBandSlots * G_NI);  // band window states
+    if (PERC && (int)lane < kBandSlots) btag[lane * G_NI + G_CNT] = 0;  // nothing cached
     const int32_t n_last = M.n_max - 1;
+    // A band window starting at step n runs up to K steps if the reading index
+    // n + L is even, else K - 1 (a fresh batch of readings starts at the even
+    // index below n + L): the length never depends on what the slot holds.
+    auto band_len = [&](int32_t n) { return AEB_FP32_WINDOW - (int)((n + F.plat) & 1); };
+    // where the readings of a band lane's step n are in its slot
+    auto band_rd = [&](int sl, int32_t n) {
+        return rdg + sl * kBandCache + (n - btag[sl * G_NI + G_STEP]);
+    };
 
     Tile tile{};
     int cursor = 0, bcount = 0;
@@ -1011,7 +1073,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         bool ended = false;
         float vl1, gl1;  // end-of-step low words of a slow step that ended
         int tlen = AEB_FP32_WINDOW;  // steps before the next TTC test
-        int slot = -1, trel = -1;    // per-step perception: readings slot, trigger step
+        int slot = -1;               // per-step perception: the lane's band slot
         bool wait = false;           // per-step perception: a band lane waiting for a slot
         if (TTC && active && !L.trig) {
             tlen = L.ci(L_NCHK) - L.n;  // steps the last test still covers
@@ -1027,30 +1089,65 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
         }
         if (PERC) {
             // Lanes in their noise band (every step needs its reading): up to
-            // kBandSlots of them get the readings of their next K steps,
-            // generated at full warp width (one Philox block per lane), and
-            // test the trigger inside their window; the others wait for a
+            // kBandSlots of them get a slot that holds their readings, and run
+            // windows with the trigger tested inside; the others wait for a
             // later pass (so that a sample's windows, and its arithmetic, never
             // depend on the lanes it shares a warp with), and a lane at its
-            // last step (no window) tests that step alone.
+            // last step (no window) tests that step alone.  Readings are
+            // generated at full warp width, two per Philox block per thread:
+            // a slot whose tag does not cover the lane's next band window
+            // (band_len) gets 2K readings from the whole warp if it is alone,
+            // else K from a half-warp, starting at the lane's step (one
+            // earlier if that step's reading index is odd: a block holds an
+            // even and an odd reading).
             const bool band = active && !L.trig && tlen <= 0;
             const unsigned bm = __ballot_sync(kFull, band && !L.at_slow(n_last));
             if (bm) {
                 const int rank = __popc(bm & lanemask_lt());
                 if (((bm >> lane) & 1u) && rank < kBandSlots) slot = rank;
-                const int nb = __popc(bm) < kBandSlots ? __popc(bm) : kBandSlots;
                 const int klo = L.ci(L_KIDXLO), khi = L.ci(L_KIDXHI);
-                const float sgl = L.cf(L_SIGMA);
-                unsigned rest = bm;
-                for (int sb = 0; sb < nb; ++sb) {
-                    const int src = __ffs(rest) - 1;
-                    rest &= rest - 1;
-                    const uint64_t kr = (uint64_t)(uint32_t)__shfl_sync(kFull, klo, src) |
-                                        ((uint64_t)(uint32_t)__shfl_sync(kFull, khi, src) << 32);
-                    const int32_t ns = __shfl_sync(kFull, L.n, src);
-                    const float sig = __shfl_sync(kFull, sgl, src);
-                    const float r = L.reading(F, kr, ns + (int32_t)lane, sig);
-                    if ((int)lane < AEB_FP32_WINDOW) rdg[sb * AEB_FP32_WINDOW + lane] = r;
+                bool miss = false;
+                if (slot >= 0) {
+                    const int *tg = btag + slot * G_NI;
+                    miss = !(tg[G_KLO] == klo && tg[G_KHI] == khi && tg[G_STEP] <= L.n &&
+                             L.n + band_len(L.n) <= tg[G_STEP] + tg[G_CNT]);
+                }
+                unsigned mm = __ballot_sync(kFull, miss);
+                if (mm) {
+                    __syncwarp();  // the last window's reads of the slots come first
+                    const int g = __popc(mm);
+                    const int par = (int)((L.n + F.plat) & 1);
+                    if (miss) {  // the schedule below: pairs in rank order, a last single
+                        const int iota = __popc(mm & lanemask_lt());
+                        int *tg = btag + slot * G_NI;
+                        tg[G_KLO] = klo;
+                        tg[G_KHI] = khi;
+                        tg[G_STEP] = L.n - par;
+                        tg[G_CNT] = ((g & 1) && iota == g - 1) ? kBandCache : AEB_FP32_WINDOW;
+                    }
+                    const float sgl = L.cf(L_SIGMA);
+                    const int hw = (int)(lane >> 4);
+                    while (mm) {
+                        const int sa = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        const bool pair = mm != 0;
+                        const int sbb = pair ? __ffs(mm) - 1 : sa;
+                        if (pair) mm &= mm - 1;
+                        const int src = (pair && hw) ? sbb : sa;
+                        const uint64_t kr = (uint64_t)(uint32_t)__shfl_sync(kFull, klo, src) |
+                                            ((uint64_t)(uint32_t)__shfl_sync(kFull, khi, src) << 32);
+                        const int32_t ns = __shfl_sync(kFull, L.n, src);
+                        const float sig = __shfl_sync(kFull, sgl, src);
+                        const int ss = __shfl_sync(kFull, slot, src);
+                        // block q of this slot's batch: readings 2q, 2q + 1 of its cache
+                        const int q = pair ? (int)(lane & 15u) : (int)lane;
+                        const long long r0 = (long long)ns + F.plat;
+                        float ra, rb;
+                        L.reading_pair(F, kr, (uint64_t)(r0 >> 1) + (uint64_t)q, sig, ra, rb);
+                        float *rs = rdg + ss * kBandCache;
+                        rs[2 * q] = ra;
+                        rs[2 * q + 1] = rb;
+                    }
                 }
                 __syncwarp();
             }
@@ -1075,19 +1172,66 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
             }
             // a lane already at a slow step runs no window in this pass
             if (active)
-                len = (wait || L.at_slow(n_last)) ? 0
-                                                  : L.window_len(slot >= 0 ? AEB_FP32_WINDOW : tlen);
+                len = (wait || L.at_slow(n_last)) ? 0 : L.window_len(slot >= 0 ? band_len(L.n) : tlen);
             // (a lane with readings tests its trigger in the band window, never
             // in the unrolled full one)
             full = __all_sync(kFull, len == AEB_FP32_WINDOW && slot < 0);
         }
         bool replay = false;
         if (full) {
-            if (active) replay = L.template step_window<true>(F, len);
+            // (the perception kernels, whose readings and band code already
+            // fill the instruction cache, run it through the rolled loop: the
+            // unrolled copy costs them more in cache misses than it saves)
+            if (active) replay = L.template step_window<!PERC>(F, len);
         } else if (PERC && __any_sync(kFull, slot >= 0)) {
-            if (active && len > 0)
-                replay = L.step_window_band(F, len, slot >= 0 ? rdg + slot * AEB_FP32_WINDOW : nullptr,
-                                            trel, n_last);
+            // Band lanes keep their window's states; then the warp tests each
+            // band lane's trigger at all the window's steps at once (lane j:
+            // step j, with the margin's window-constant parts and the
+            // readings of the band lane).  The first step that fires is the
+            // trigger; if its onset falls inside the window, the lane goes
+            // back to the window's start and, triggered, runs up to the onset
+            // in the next pass, the window the trigger test inside the loop
+            // would have cut (the same steps, so the same arithmetic).
+            float *st = (slot >= 0 && len > 0) ? sst + slot * kBandState : nullptr;
+            float thr_h = 0.0f, c1 = 0.0f, hk = 0.0f;
+            if (st) L.band_consts(thr_h, c1, hk);
+            const int32_t n0 = L.n;
+            if (active && len > 0) replay = L.step_window_st(F, len, st);
+            __syncwarp();
+            unsigned tm = __ballot_sync(kFull, st != nullptr);
+            int tr = -1;
+            const float sl = LEAD == kLeadMoving ? L.cf(L_S) : 0.0f;
+            const float sg = LEAD == kLeadMoving ? L.cf(L_SIGMA) : 0.0f;
+            while (tm) {
+                const int src = __ffs(tm) - 1;
+                tm &= tm - 1;
+                const int ss = __shfl_sync(kFull, slot, src);
+                const int ln = __shfl_sync(kFull, len, src);
+                const int32_t m0 = __shfl_sync(kFull, n0, src);
+                const float th = __shfl_sync(kFull, thr_h, src);
+                const float cc = __shfl_sync(kFull, c1, src);
+                const float hh = __shfl_sync(kFull, hk, src);
+                const float ssl = __shfl_sync(kFull, sl, src);
+                const float ssg = __shfl_sync(kFull, sg, src);
+                bool f = false;
+                if ((int)lane < ln) {
+                    const float *sp = sst + ss * kBandState;
+                    float m = (sp[lane] + hh) - fmaf(th, sp[AEB_FP32_WINDOW + lane], cc);
+                    if (LEAD == kLeadMoving)
+                        m = m + fmaf(th, L.lead_speed(F, m0 + (int32_t)lane, ssl),
+                                     L.lead_gap(F, m0 + (int32_t)lane, ssg));
+                    f = m + band_rd(ss, m0)[lane] <= 0.0f;  // a missing reading never fires
+                }
+                const unsigned fb = __ballot_sync(kFull, f);
+                if ((int)lane == src && fb) tr = __ffs(fb) - 1;
+            }
+            if (tr >= 0) {
+                L.fire(F, n0 + tr, n_last);
+                if (L.ev - n0 < len) {  // the onset falls inside the window
+                    L.band_rewind(st, n0);
+                    replay = false;
+                }
+            }
         } else {
             if (active && len > 0) replay = L.template step_window<false>(F, len);
         }
@@ -1132,7 +1276,10 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     bf[B_NMP * 32 + j] = L.nmP;
                     bf[B_C * 32 + j] = L.C;
                     bi[B_N * 32 + j] = L.n;
-                    bi[B_LEN * 32 + j] = len | ((trel + 1) << 8);  // + a trigger in the window
+                    // + the step of a trigger inside the window (from the
+                    // test-step field; the flush drops a trigger after the end)
+                    const int trel = (PERC && L.trig && L.ci(L_NCHK) >= L.n) ? L.ci(L_NCHK) - L.n : -1;
+                    bi[B_LEN * 32 + j] = len | ((trel + 1) << 8);
                 } else {
                     bf[B_G1H * 32 + j] = L.gh;
                     bf[B_G1L * 32 + j] = gl1;
@@ -1168,7 +1315,7 @@ ModelF32 to_f32(const ModelDev &m)
     f.lts = (float)m.lead_ts;
     f.lxs = (float)m.lead_xs;
     f.psig = (float)m.perc_sigma;
-    f.pdrop = (float)m.perc_drop;
+    f.pdrop_h = (uint64_t)std::ceil(m.perc_drop * 4294967296.0);  // perc_drop in [0, 1]
     f.pseed = m.perc_seed;
     f.plat = m.perc_lat;
     f.perc = m.perc;

@@ -237,11 +237,11 @@ struct Lane64 {
             }
             bool reading = true;
             if (M.perc) {  // the reading of step n + L describes step n
-                uint64_t c[4] = {row, (uint64_t)((long long)n + M.perc_lat), 0, 0};
-                philox_block(c, M.perc_seed, kPercKey1);
-                const double s53 = 1.0 / 9007199254740992.0;  // 2^-53
-                const double u1 = (double)(c[0] >> 11) * s53, u2 = (double)(c[1] >> 11) * s53;
-                const double u3 = (double)(c[2] >> 11) * s53, u4 = (double)(c[3] >> 11) * s53;
+                uint32_t h[4];
+                perc_halves(row, (uint64_t)((long long)n + M.perc_lat), M.perc_seed, h);
+                const double s32 = 1.0 / 4294967296.0;  // 2^-32
+                const double u1 = (double)h[0] * s32, u2 = (double)h[1] * s32;
+                const double u3 = (double)h[2] * s32, u4 = (double)h[3] * s32;
                 if (u4 < M.perc_drop) reading = false;
                 else gap_meas = gap_meas + M.perc_sigma * (2.0 * (((u1 + u2) + u3) - 1.5));
             }

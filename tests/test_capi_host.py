@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(aeb):
     L = C.CDLL(aeb._build.LIB)
     for n in names:
         assert hasattr(L, n), n
-    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 5
+    assert aeb.lib().aeb_abi_version() == aeb.ABI_VERSION == 6
 
 
 def test_struct_layouts_match_header(aeb, tmp_path):

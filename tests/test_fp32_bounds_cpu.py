@@ -18,7 +18,7 @@ from fp32_bounds import fp32_report, resolve_onset_ties, with_gap
 CASES = {
     "ttc_2s": (ai.ttc_model(thr=2.0), ai.single_scenario(seed=90), 20_000),
     "ttc_perception": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=0.8, perc_drop=0.2,
-                                  perc_latency=0.05, perc_seed=3),
+                                  perc_latency=0.05, perc_seed=4),
                        ai.single_scenario(seed=91), 20_000),
     "moving_lead_ttc": (ai.replace(ai.lead_braking_model(lead_decel=4.0), trigger=ai.TRIGGER_TTC,
                                    ttc_thr=3.0), ai.lead_braking_scenario(seed=92), 20_000),

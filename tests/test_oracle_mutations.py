@@ -42,8 +42,11 @@ MUTATIONS = [
     ("lead never stops", "if (t >= ts) return 0.5 * (vl * ts);",
      "if (t >= ts + 1e9) return 0.5 * (vl * ts);"),
     ("impact speed not relative", "c1 = vn - lead_speed(m, t1);", "c1 = vn;"),
-    ("perception word", "double u3 = (double)(w[2] >> 11) * two_m53",
-     "double u3 = (double)(w[1] >> 11) * two_m53"),
+    ("perception word", "double u3 = (double)((w[2] >> sh) & 0xffffffffULL) * two_m32;",
+     "double u3 = (double)((w[1] >> sh) & 0xffffffffULL) * two_m32;"),
+    ("perception half", "const int sh = (k & 1) ? 0 : 32;", "const int sh = (k & 1) ? 32 : 0;"),
+    ("perception pair block", "uint64_t ctr[4] = {row, (uint64_t)k >> 1, 0, 0}",
+     "uint64_t ctr[4] = {row, (uint64_t)k, 0, 0}"),
     ("dropout sense", "if (u4 < m->perc_drop) return 0;", "if (u4 > m->perc_drop) return 0;"),
     ("latency onset", "n_b = (n + lat) + c->n_delay;", "n_b = n + c->n_delay;"),
     ("reading index", "reading = perception(m, row, n + lat, &pn);",

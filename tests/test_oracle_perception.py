@@ -13,13 +13,16 @@ import aeb_inputs as ai
 from test_oracle_rng import numpy_philox_block
 
 PERC_KEY1 = 0x5045524345505431  # "PERCEPT1"
-TWO_M53 = 2.0 ** -53
+TWO_M32 = 2.0 ** -32
 
 
 def numpy_reading(m, row, k):
-    """(present, noise) of the reading of step k from numpy's Philox."""
-    w = numpy_philox_block([row, k, 0, 0], [m.perc_seed, PERC_KEY1])
-    u = [float(int(x) >> 11) * TWO_M53 for x in w]
+    """(present, noise) of the reading of step k from numpy's Philox: block
+    (row, k // 2, 0, 0); even k takes the words' high 32-bit halves, odd k
+    the low halves."""
+    w = numpy_philox_block([row, k // 2, 0, 0], [m.perc_seed, PERC_KEY1])
+    h = [(int(x) >> 32) if k % 2 == 0 else (int(x) & 0xFFFFFFFF) for x in w]
+    u = [float(x) * TWO_M32 for x in h]
     if u[3] < m.perc_drop:
         return False, 0.0
     return True, m.perc_sigma * (2.0 * (((u[0] + u[1]) + u[2]) - 1.5))
@@ -35,9 +38,19 @@ def irwin_hall3_cdf(s):
 def test_readings_match_numpy_philox(oracle_mod):
     m = ai.Model(trigger=ai.TRIGGER_TTC, perc_sigma=0.7, perc_drop=0.25, perc_seed=991)
     rng = np.random.default_rng(5)
-    for row, k in [(0, 0), (0, 1), (1, 0), (2 ** 40, 17)] + [
+    for row, k in [(0, 0), (0, 1), (0, 2), (0, 3), (1, 0), (2 ** 40, 17), (5, 2 ** 33 + 1)] + [
             (int(r), int(k)) for r, k in zip(rng.integers(0, 2 ** 40, 60), rng.integers(0, 10 ** 6, 60))]:
         assert oracle_mod.perception(m, row, k) == numpy_reading(m, row, k), (row, k)
+
+
+def test_paired_readings_are_independent(oracle_mod):
+    """Readings 2j and 2j + 1 share a block but not its bits: across many
+    pairs their noises are uncorrelated and each pair differs."""
+    m = ai.Model(trigger=ai.TRIGGER_TTC, perc_sigma=1.0, perc_drop=0.0, perc_seed=12)
+    a = np.array([oracle_mod.perception(m, 3, 2 * j)[1] for j in range(4000)])
+    b = np.array([oracle_mod.perception(m, 3, 2 * j + 1)[1] for j in range(4000)])
+    assert np.all(a != b)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4.5 / math.sqrt(len(a))
 
 
 def test_noise_distribution_and_dropout(oracle_mod):

@@ -25,14 +25,16 @@ seeded inputs.
         sample: at the step where the binary32 kernel fired and the oracle did
         not, the oracle's binary64 margin (gap + noise) - thr closing speed is
         <= eps; at every step where the oracle fired and the kernel did not,
-        the margin is >= -eps (or the reading's dropout decision is a tie:
-        |u4 - perc_drop| <= 2^-23).  eps = 2^-21 (|gap + noise| + thr |closing|
-        + x_n + d0 + x_L + thr v_L) + 12 2^-24 perc_sigma: eight binary32
-        ulps of every quantity the kernel rounds on the way to the margin (the
-        compensated state carries <= ~6 ulps of position through the approach,
-        each operand of the margin one rounding, the lead's closed form in
-        binary32 about three, the reading's 24-bit uniforms 6 2^-24 sigma
-        plus its arithmetic).  Such a sample is then compared, with every
+        the margin is >= -eps (a reading's dropout decision is the oracle's
+        exactly: an integer comparison of its word with ceil(perc_drop 2^32)).
+        eps = 2^-21 (|gap + noise| + thr |closing| + x_n + d0 + x_L + thr v_L)
+        + 18 2^-24 perc_sigma: eight binary32 ulps of every quantity the kernel
+        rounds on the way to the margin (the compensated state carries <= ~6
+        ulps of position through the approach, each operand of the margin one
+        rounding, the lead's closed form in binary32 about three), and for the
+        reading's noise 6 2^-24 sigma from the 24-bit uniforms (the oracle's
+        have 32 bits), 6 from the two roundings of their sum, 6 from the two
+        products that scale it.  Such a sample is then compared, with every
         bound above, against the oracle run with its trigger forced to the
         kernel's step: no sample escapes the bounds.
   * aeb_reduce: integer counts and histograms exact, extremes exact, sums
