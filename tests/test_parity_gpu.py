@@ -119,6 +119,13 @@ FP64_CASES = {
     "moving_lead_ttc_5ms": (ai.replace(ai.lead_braking_model(dt=5e-3, lead_decel=4.0),
                                        trigger=ai.TRIGGER_TTC, ttc_thr=3.0),
                             ai.lead_braking_scenario(seed=34), 3_000),
+    # a wide noise band (many lanes in it at once) at an odd latency; every
+    # reading missing (the trigger never fires)
+    "ttc_perception_wide": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=4.0, perc_drop=0.5,
+                                       perc_latency=0.021, perc_seed=41),
+                            ai.single_scenario(seed=41), 3_000),
+    "ttc_perception_all_missing": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=1.0, perc_drop=1.0,
+                                              perc_seed=42), ai.single_scenario(seed=42), 2_000),
 }
 
 
@@ -190,6 +197,19 @@ FP32_CASES = {
     "moving_lead_ttc_5ms": (ai.replace(ai.lead_braking_model(dt=5e-3, lead_decel=4.0),
                                        trigger=ai.TRIGGER_TTC, ttc_thr=3.0),
                             ai.lead_braking_scenario(seed=36), 10_000),
+    # per-step perception: the band windows' trigger tests with a moving lead's
+    # terms (odd latency: 31-step band windows from odd reading indices), a
+    # wide band (more band lanes than slots: waits, shared reading batches),
+    # every reading missing
+    "moving_lead_ttc_perception": (ai.replace(ai.lead_braking_model(lead_decel=4.0),
+                                              trigger=ai.TRIGGER_TTC, ttc_thr=3.0, perc_sigma=1.5,
+                                              perc_drop=0.4, perc_latency=0.0123, perc_seed=14),
+                                   ai.lead_braking_scenario(seed=37), 10_000),
+    "ttc_perception_wide": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=4.0, perc_drop=0.5,
+                                       perc_latency=0.021, perc_seed=43),
+                            ai.single_scenario(seed=43), 10_000),
+    "ttc_perception_all_missing": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=1.0, perc_drop=1.0,
+                                              perc_seed=44), ai.single_scenario(seed=44), 5_000),
 }
 
 
