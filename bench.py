@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--ttc-thr", type=float, default=None,
                     help="brake on the TTC trigger at this threshold (s) instead of "
                          "immediately (same samples; for profiling the TTC kernel)")
+    ap.add_argument("--perception", action="store_true",
+                    help="with --ttc-thr: per-step readings (1 m noise, 20 %% dropout, 50 ms "
+                         "latency), as in the perception line (for profiling its kernel)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -444,8 +447,7 @@ def perception_run(aeb, torch):
     O = aeb.alloc_outputs(N, which=("status", "x_ref", "v_imp", "n_steps"))
     out = {}
     for name, m in (("plain", base),
-                    ("perception", ai.replace(base, perc_sigma=1.0, perc_drop=0.2,
-                                              perc_latency=0.05, perc_seed=1))):
+                    ("perception", ai.replace(base, **PERCEPTION))):
         aeb.aeb_rollout(m, P, N, aeb.FP32_COMP, O)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -566,14 +568,20 @@ def pooled_stats(aeb, torch, dist, S, world, dev):
             "how": "all_gather of aeb_stats, aeb_stats_merge in rank order"}
 
 
+PERCEPTION = dict(perc_sigma=1.0, perc_drop=0.2, perc_latency=0.05, perc_seed=1)
+
+
 def model_of(args):
     if args.ttc_thr is not None:
-        return ai.ttc_model(thr=args.ttc_thr, dt=args.dt)
+        m = ai.ttc_model(thr=args.ttc_thr, dt=args.dt)
+        return ai.replace(m, **PERCEPTION) if args.perception else m
     return ai.single_model(dt=args.dt)
 
 
 def config(args, world, precision="fp32-compensated"):
     trig = "immediate trigger" if args.ttc_thr is None else f"TTC trigger at {args.ttc_thr:g} s"
+    if args.ttc_thr is not None and args.perception:
+        trig += " with per-step readings (1 m noise, 20 % dropout, 50 ms latency)"
     return {"workload": f"single scenario, N={args.n} samples per GPU, dt={args.dt * 1e3:g} ms, "
                         f"10 s horizon, lead at d0, per-axle caps, {trig}",
             "n_samples_per_gpu": args.n, "dt_s": args.dt, "precision": precision,
