@@ -450,6 +450,28 @@ aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *params, uint64
                         aeb_stats *host_stats, const aeb_outputs *host_out, void *stream);
 
 /*
+ * aeb_evaluate_scenario -- the whole path from the seed (Sec. IV-C sampling,
+ * then the rollout and reduction of aeb_evaluate): samples first .. first+n-1
+ * of `scenario` are drawn on the host in chunks of 2^20 into pinned staging
+ * buffers owned by the library, and each chunk is uploaded and rolled out
+ * while the host draws the next one; then the reduction and the copy of the
+ * stats back.  Results are the same bits as aeb_sample_params(first, n) into
+ * host columns followed by aeb_evaluate of those n samples (sample i keeps row
+ * i for its perception readings).
+ *   n_threads   host sampling threads (0: all hardware threads)
+ *   host_stats  host aeb_stats written on success
+ * The device buffers, two staging buffers of 2^20 samples, internal streams
+ * and events are kept per (device, stream) as for aeb_evaluate; calls on the
+ * same stream from several threads must be serialised by the caller.
+ * Synchronous.  AEB_EINVAL for a bad model, scenario, precision or histogram
+ * spec (nothing runs); AEB_ENOMEM if the buffers cannot be grown.
+ */
+aeb_status aeb_evaluate_scenario(const aeb_model *model, const aeb_scenario *scenario,
+                                 uint64_t first, uint64_t n, aeb_precision precision,
+                                 const aeb_hist_spec *hist, int32_t n_threads,
+                                 aeb_stats *host_stats, void *stream);
+
+/*
  * aeb_batch_create -- plan a batched launch over n_jobs jobs (the per-sample
  * method is that of aeb_rollout, Sec. IV-D, V-A..V-D).  Builds
  * the table of (job, tile) work items, allocates the device tables and

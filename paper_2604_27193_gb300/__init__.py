@@ -185,6 +185,9 @@ def lib():
                                      C.c_void_p]
             L.aeb_evaluate.argtypes = [P(Model), P(Params), C.c_uint64, C.c_int32,
                                        P(HistSpec), P(Stats), P(Outputs), C.c_void_p]
+            L.aeb_evaluate_scenario.argtypes = [P(Model), P(Scenario), C.c_uint64, C.c_uint64,
+                                                C.c_int32, P(HistSpec), C.c_int32, P(Stats),
+                                                C.c_void_p]
             L.aeb_batch_create.argtypes = [P(Model), P(Job), C.c_uint32, P(Params), C.c_int32,
                                            P(Outputs), C.c_void_p, P(C.c_void_p)]
             L.aeb_batch_run.argtypes = [C.c_void_p, C.c_void_p]
@@ -218,7 +221,7 @@ def lib():
                        "aeb_serve_cancel", "aeb_serve_counters_get", "aeb_sample_params_is",
                        "aeb_reduce_weighted", "aeb_stats_summary", "aeb_job_stats_summary",
                        "aeb_hist_quantile", "aeb_hist_exceedance", "aeb_is_estimate",
-                       "aeb_serve_inject_faults"):
+                       "aeb_serve_inject_faults", "aeb_evaluate_scenario"):
                 getattr(L, fn).restype = C.c_int32
             if L.aeb_abi_version() != ABI_VERSION:
                 raise ImportError("libaeb.so ABI version mismatch")
@@ -382,6 +385,17 @@ def aeb_evaluate(m, params_host: dict, n: int, precision: int, hist: HistSpec,
     _check(lib().aeb_evaluate(C.byref(ms), C.byref(ps), n, precision, C.byref(hist),
                               C.byref(st), C.byref(os_) if os_ is not None else None,
                               _stream(stream)))
+    return st
+
+
+def aeb_evaluate_scenario(m, sc, first: int, n: int, precision: int, hist: HistSpec,
+                          n_threads: int = 0, stream=None) -> Stats:
+    """Whole path from the seed (host sampling overlapped with the upload and
+    rollout of the previous chunk); returns the stats (synchronous)."""
+    ms, ss = model(m), scenario(sc)
+    st = Stats()
+    _check(lib().aeb_evaluate_scenario(C.byref(ms), C.byref(ss), first, n, precision,
+                                       C.byref(hist), n_threads, C.byref(st), _stream(stream)))
     return st
 
 

@@ -242,11 +242,17 @@ aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &
 constexpr int kEvalMaxChunks = 12;
 constexpr uint64_t kEvalFirstChunk = uint64_t(1) << 18;
 constexpr uint64_t kEvalGrow = 2;
+// aeb_evaluate_scenario draws chunks of kSampledChunk samples on the host into
+// two pinned staging buffers (pin[k % 2]); the upload of chunk k records
+// uploaded[k % 2], after which the host may draw chunk k + 2 into that buffer.
+constexpr uint64_t kSampledChunk = uint64_t(1) << 20;
 struct EvalBuffers {
     void *base = nullptr;
     uint64_t cap = 0;  // samples
     cudaStream_t copy = nullptr, comp[2] = {nullptr, nullptr};
     cudaEvent_t start = nullptr, copied[kEvalMaxChunks] = {}, done[2] = {nullptr, nullptr};
+    double *pin[2] = {nullptr, nullptr};  // AEB_NFIELDS columns of kSampledChunk each
+    cudaEvent_t uploaded[2] = {nullptr, nullptr};
 };
 
 cudaError_t eval_streams(EvalBuffers &b)
@@ -260,6 +266,8 @@ cudaError_t eval_streams(EvalBuffers &b)
         e = cudaEventCreateWithFlags(&b.copied[i], cudaEventDisableTiming);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&b.done[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&b.uploaded[i], cudaEventDisableTiming);
     return e;
 }
 std::map<std::pair<int, uintptr_t>, EvalBuffers> g_eval;
@@ -267,6 +275,65 @@ std::map<std::pair<int, uintptr_t>, EvalBuffers> g_eval;
 constexpr size_t kEvalBytesPerSample = 8 * AEB_NFIELDS + 1 + 8 * 4 + 4 * 2;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The evaluate buffers of (current device, s), grown to at least cap samples.
+aeb_status eval_acquire(cudaStream_t s, uint64_t cap, EvalBuffers **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    EvalBuffers &b = g_eval[{dev, reinterpret_cast<uintptr_t>(s)}];
+    e = eval_streams(b);
+    if (e != cudaSuccess) return cuda_fail(e, "evaluate: streams");
+    if (b.cap < cap) {
+        if (b.base) {
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(b.base);
+            b.base = nullptr;
+            b.cap = 0;
+        }
+        const size_t bytes = align256(sizeof(aeb_stats)) + cap * kEvalBytesPerSample + 16 * 256;
+        e = cudaMalloc(&b.base, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(evaluate buffers)");
+        b.cap = cap;
+    }
+    *out = &b;
+    return AEB_OK;
+}
+
+// The device stats, parameter columns and outputs of n <= b.cap samples in
+// the buffers of b.
+struct EvalLayout {
+    aeb_stats *stats;
+    aeb_params params;
+    aeb_outputs out;
+};
+EvalLayout eval_layout(const EvalBuffers &b)
+{
+    const uint64_t cap = b.cap;
+    char *p = static_cast<char *>(b.base);
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += align256(bytes);
+        return r;
+    };
+    EvalLayout L;
+    L.stats = reinterpret_cast<aeb_stats *>(take(sizeof(aeb_stats)));
+    double **dcols[AEB_NFIELDS] = {&L.params.v0, &L.params.d0, &L.params.mu, &L.params.gs,
+                                   &L.params.gc, &L.params.mass, &L.params.cd, &L.params.tau,
+                                   &L.params.t_delay, &L.params.noise};
+    for (int j = 0; j < AEB_NFIELDS; ++j) *dcols[j] = reinterpret_cast<double *>(take(8 * cap));
+    L.out.status = reinterpret_cast<uint8_t *>(take(cap));
+    L.out.x_raw = reinterpret_cast<double *>(take(8 * cap));
+    L.out.x_ref = reinterpret_cast<double *>(take(8 * cap));
+    L.out.v_imp = reinterpret_cast<double *>(take(8 * cap));
+    L.out.t_end = reinterpret_cast<double *>(take(8 * cap));
+    L.out.n_steps = reinterpret_cast<int32_t *>(take(4 * cap));
+    L.out.n_onset = reinterpret_cast<int32_t *>(take(4 * cap));
+    return L;
+}
 
 }  // namespace
 
@@ -373,52 +440,14 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
     if (!host_stats) return fail(AEB_EINVAL, "aeb_evaluate: host_stats is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    const uint64_t cap = n > 0 ? n : 1;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    void *base = nullptr;
     EvalBuffers *eb = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        EvalBuffers &b = g_eval[{dev, reinterpret_cast<uintptr_t>(s)}];
-        e = eval_streams(b);
-        if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: streams");
-        eb = &b;
-        if (b.cap < cap) {
-            if (b.base) {
-                e = cudaStreamSynchronize(s);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-                cudaFree(b.base);
-                b.base = nullptr;
-                b.cap = 0;
-            }
-            const size_t bytes = align256(sizeof(aeb_stats)) + cap * kEvalBytesPerSample + 16 * 256;
-            e = cudaMalloc(&b.base, bytes);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(evaluate buffers)");
-            b.cap = cap;
-        }
-        base = b.base;
-    }
-    char *p = static_cast<char *>(base);
-    auto take = [&](size_t bytes) {
-        char *r = p;
-        p += align256(bytes);
-        return r;
-    };
-    aeb_stats *dstats = reinterpret_cast<aeb_stats *>(take(sizeof(aeb_stats)));
-    aeb_params dp;
-    double **dcols[AEB_NFIELDS] = {&dp.v0, &dp.d0, &dp.mu, &dp.gs, &dp.gc,
-                                   &dp.mass, &dp.cd, &dp.tau, &dp.t_delay, &dp.noise};
-    for (int j = 0; j < AEB_NFIELDS; ++j) *dcols[j] = reinterpret_cast<double *>(take(8 * cap));
-    aeb_outputs dout;
-    dout.status = reinterpret_cast<uint8_t *>(take(cap));
-    dout.x_raw = reinterpret_cast<double *>(take(8 * cap));
-    dout.x_ref = reinterpret_cast<double *>(take(8 * cap));
-    dout.v_imp = reinterpret_cast<double *>(take(8 * cap));
-    dout.t_end = reinterpret_cast<double *>(take(8 * cap));
-    dout.n_steps = reinterpret_cast<int32_t *>(take(4 * cap));
-    dout.n_onset = reinterpret_cast<int32_t *>(take(4 * cap));
+    st = eval_acquire(s, n > 0 ? n : 1, &eb);
+    if (st != AEB_OK) return st;
+    const EvalLayout lay = eval_layout(*eb);
+    aeb_stats *dstats = lay.stats;
+    const aeb_params dp = lay.params;
+    const aeb_outputs dout = lay.out;
+    cudaError_t e = cudaSuccess;
 
     ParamsDev pd;
     check_params(&dp, &pd);
@@ -485,6 +514,95 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(outputs)");
         }
     }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return AEB_OK;
+}
+
+extern "C" aeb_status aeb_evaluate_scenario(const aeb_model *model, const aeb_scenario *scenario,
+                                            uint64_t first, uint64_t n, aeb_precision precision,
+                                            const aeb_hist_spec *hist, int32_t n_threads,
+                                            aeb_stats *host_stats, void *stream)
+{
+    clear_error();
+    ModelDev md;
+    aeb_status st = check_model(model, &md);
+    if (st != AEB_OK) return st;
+    if (precision != AEB_FP64_PLAIN && precision != AEB_FP32_COMP)
+        return fail(AEB_EINVAL, "unknown precision");
+    st = check_hist(hist);
+    if (st != AEB_OK) return st;
+    if (!host_stats) return fail(AEB_EINVAL, "aeb_evaluate_scenario: host_stats is NULL");
+    {  // the scenario's checks (no samples drawn)
+        aeb_params none;
+        std::memset(&none, 0, sizeof none);
+        st = aeb_sample_params(model, scenario, first, 0, &none, n_threads);
+        if (st != AEB_OK) return st;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EvalBuffers *eb = nullptr;
+    st = eval_acquire(s, n > 0 ? n : 1, &eb);
+    if (st != AEB_OK) return st;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2; ++i) {
+        if (eb->pin[i]) continue;
+        void *h = nullptr;
+        e = cudaHostAlloc(&h, sizeof(double) * AEB_NFIELDS * kSampledChunk, cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc(sampling staging)");
+        eb->pin[i] = static_cast<double *>(h);
+    }
+    const EvalLayout lay = eval_layout(*eb);
+    ParamsDev pd;
+    check_params(&lay.params, &pd);
+    if (n > 0) {
+        aeb_outputs want = lay.out;
+        want.x_raw = nullptr;
+        want.t_end = nullptr;
+        want.n_onset = nullptr;
+        const OutDev od = out_dev(&want);
+        // the copies start after the work already queued on the caller's stream
+        e = cudaEventRecord(eb->start, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(eb->copy, eb->start, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate_scenario: stream order");
+        const uint64_t chunks = (n + kSampledChunk - 1) / kSampledChunk;
+        for (uint64_t k = 0; k < chunks; ++k) {
+            const uint64_t off = k * kSampledChunk;
+            const uint64_t len = n - off < kSampledChunk ? n - off : kSampledChunk;
+            const int b = (int)(k % 2);
+            if (k >= 2) {  // the upload of chunk k - 2 from this buffer has ended
+                e = cudaEventSynchronize(eb->uploaded[b]);
+                if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate_scenario: staging");
+            }
+            aeb_params hp;
+            double **hc[AEB_NFIELDS] = {&hp.v0, &hp.d0, &hp.mu, &hp.gs, &hp.gc,
+                                        &hp.mass, &hp.cd, &hp.tau, &hp.t_delay, &hp.noise};
+            for (int j = 0; j < AEB_NFIELDS; ++j) *hc[j] = eb->pin[b] + (size_t)j * kSampledChunk;
+            st = aeb_sample_params(model, scenario, first + off, len, &hp, n_threads);
+            if (st != AEB_OK) return st;
+            ParamsDev pk = pd;
+            for (int j = 0; j < AEB_NFIELDS; ++j) {
+                e = cudaMemcpyAsync(const_cast<double *>(pd.col[j]) + off, *hc[j], 8 * len,
+                                    cudaMemcpyHostToDevice, eb->copy);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(params)");
+                pk.col[j] = pd.col[j] + off;
+            }
+            cudaStream_t cs = eb->comp[b];
+            e = cudaEventRecord(eb->uploaded[b], eb->copy);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, eb->uploaded[b], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate_scenario: chunk order");
+            st = rollout_impl(md, pk, len, precision, offset_out(od, off), cs, off);
+            if (st != AEB_OK) return st;
+        }
+        for (int i = 0; i < 2; ++i) {
+            e = cudaEventRecord(eb->done[i], eb->comp[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, eb->done[i], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate_scenario: join");
+        }
+    }
+    st = reduce_impl(&lay.out, n, *hist, lay.stats, s);
+    if (st != AEB_OK) return st;
+    e = cudaMemcpyAsync(host_stats, lay.stats, sizeof(aeb_stats), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(stats)");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return AEB_OK;
