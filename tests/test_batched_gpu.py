@@ -119,6 +119,43 @@ def test_batched_fp32_alone_equals_in_mix(aeb):
     assert sum(s.n for s in stats) == total
 
 
+PERC = dict(trigger=ai.TRIGGER_TTC, ttc_thr=2.0, perc_sigma=1.2, perc_drop=0.25,
+            perc_latency=0.013, perc_seed=77)
+
+
+def test_batched_perception_key_offsets(aeb, oracle_mod):
+    """Per-step perception in a batch: job j's sample i draws its readings
+    from row key_offset_j + i.  Binary64 outputs equal the oracle run with
+    that row offset, bit for bit; FP32 outputs of each job are the same bits
+    alone (a flat launch keyed from the same row) and in the batch."""
+    m = ai.replace(ai.single_model(), **PERC)
+    params, jobs, total = grid_jobs(aeb, m, n_jobs=24, seed=13)
+    # keys: a row range of its own per job, not the parameter offset
+    jobs = [(po, oo, n, thr, 1_000_000 + 10_000 * j) for j, (po, oo, n, thr) in enumerate(jobs)]
+    P = to_dev(params)
+    out, _ = run_batched(aeb, m, jobs, P, total, aeb.FP64_PLAIN)
+    for j, job in enumerate(jobs[:10]):
+        po, oo, n, _, ko = job
+        sub = {f: params[f][po:po + n] for f in ai.FIELDS}
+        exp = oracle_mod.rollout(m, sub, threads=8, row0=ko)
+        got = job_slice(out, job[:4])
+        for k in ("status", "x_ref", "v_imp", "t_end", "n_steps", "n_onset"):
+            assert np.array_equal(bits(got[k]), bits(exp[k])), (j, k)
+    out32, _ = run_batched(aeb, m, jobs, P, total, aeb.FP32_COMP)
+    for j, job in enumerate(jobs[:10]):
+        po, oo, n, thr, ko = job
+        if n == 0:
+            continue
+        Pj = {f: P[f][po:po + n].contiguous() for f in ai.FIELDS}
+        Oj = aeb.alloc_outputs(n)
+        Sj = torch.empty(aeb.JOB_STATS_BYTES, dtype=torch.uint8, device="cuda")
+        aeb.aeb_rollout_batched(m, [(0, 0, n, thr, ko)], Pj, aeb.FP32_COMP, Oj, Sj)
+        alone = {k: v.cpu().numpy() for k, v in Oj.items()}
+        mix = job_slice(out32, job[:4])
+        for k in alone:
+            assert np.array_equal(bits(alone[k]), bits(mix[k])), (j, k)
+
+
 def test_batched_shared_params_ttc_sweep(aeb, oracle_mod):
     """Thresholds share one parameter block (the TTC sweep layout): every job
     reads the same rows, writes its own; FP64 is bit-exact per threshold and
