@@ -75,18 +75,24 @@ constexpr int kThreads = 32 * kWarps;
 #define AEB_FP32_MIN_BLOCKS 6  // resident blocks per SM the register budget must allow
 #endif
 
-// prepared per-sample record, stored field-major in shared memory (the TTC
-// fields exist only in the TTC-trigger kernel; -s dt = 2 (-s dt/2) exactly,
-// p4 = -np4 and np1 = -1 when tau > 0, else 0, are derived where needed)
+// A prepared per-sample record in the warp's tile, sample-major: the fields
+// the lane that takes the sample loads into registers (R_*), then the block it
+// keeps in its shared-memory column (C_*, copied by the whole warp when lanes
+// refill).  Integer fields are stored as their bits.  The TTC fields exist only
+// in the TTC-trigger kernel; -s dt = 2 (-s dt/2) exactly, p4 = -np4, np1 = -1
+// when tau > 0 (else 0) and (1 - mP)^(K-1) are derived where needed.
+enum { R_W0H, R_W0L, R_G0H, R_G0L, R_NH2S, R_NH6S, R_NMP, R_KIND, R_C0 };
 enum {
-    R_W0H, R_W0L, R_G0H, R_G0L, R_GS, R_S, R_NH2S, R_NH6S, R_F0, R_F1, R_R0, R_R1, R_MG,
-    R_NP2, R_NP3, R_NP4, R_NMP, R_SIGMA,
-    R_NF_BASE,                                   // float fields of every kernel
-    R_NZ = R_NF_BASE, R_THRH, R_THRL, R_NF_TTC   // TTC trigger only
+    C_NDELAY, C_GS, C_S, C_SIGMA, C_F0, C_F1, C_R0, C_R1, C_MG, C_NP2, C_NP3, C_NP4,
+    C_NBASE,                               // fields of every kernel
+    C_NZ = C_NBASE, C_THRH, C_THRL, C_NTTC  // TTC trigger only
 };
-enum { R_NDELAY, R_KIND, R_NI };  // int fields
 template <bool TTC>
-__host__ __device__ constexpr int rec_floats() { return TTC ? R_NF_TTC : R_NF_BASE; }
+__host__ __device__ constexpr int copy_fields() { return TTC ? C_NTTC : C_NBASE; }
+// Words per record: odd, so that 32 lanes reading one field of 32 records, or
+// one lane's record read by 32 lanes, hit 32 different banks.
+template <bool TTC>
+__host__ __device__ constexpr int rec_stride() { return (R_C0 + copy_fields<TTC>()) | 1; }
 enum { K_RUN = 0, K_INVALID, K_CONTACT0, K_STOP0, K_HORIZON0 };
 
 // The lead vehicle, a template parameter of the kernel (so that a stationary
@@ -101,6 +107,7 @@ struct ModelF32 {
     // moving lead: step, initial speed, deceleration, half of it, stop time,
     // stop position (binary32 copies of the model's values)
     float dt, lv0, lb, lhb, lts, lxs;
+    float idt;  // 1 / dt (first guess of the onset step)
     // per-step perception of the TTC trigger (see the model): noise scale,
     // dropout threshold on a reading's h_4 (ceil(perc_drop 2^32): h_4 below it
     // is exactly u_4 < perc_drop), latency in steps, stream key, any of them set
@@ -139,28 +146,47 @@ __device__ __forceinline__ float powi(float q)
     return r;
 }
 
-// Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
-// warp's shared slab.
-template <int LEAD, bool TTC>
-__device__ __forceinline__ void prep_tile(const ModelDev &M, const ModelF32 &F, const ParamsDev &P,
-                                          uint64_t start, int cnt, double thr, int T, float *tf,
-                                          int *ti)
+// Smallest n >= 0 with (double)n * dt >= t (clamped to 2^31 - 1), the rule of
+// steps_to_reach_dev, from a binary32 first guess t * (1/dt) instead of a
+// binary64 division (slow here); the adjustment loops make the result exact
+// whatever the guess.
+__device__ __forceinline__ int32_t steps_to_reach_f32(double t, double dt, float idt)
 {
+    if (!(t > 0.0)) return 0;
+    const float qf = ceilf(__double2float_rn(t) * idt);
+    if (!(qf < 1.0e9f)) return steps_to_reach_dev(t, dt);
+    long long n = (long long)qf;
+    while (n > 0 && (double)(n - 1) * dt >= t) --n;
+    while ((double)n * dt < t) ++n;
+    return (int32_t)n;
+}
+
+// Prepare samples [start, start + cnt) of a tile (TTC threshold thr) into the
+// warp's records (sample-major, rec_stride words each).  Kept out of line: it
+// runs once per tile, and its binary64 code inlined into the kernel cost the
+// step loop ~3 % (measured on the single-scenario workload).
+template <int LEAD, bool TTC>
+__device__ __noinline__ void prep_tile(const ModelDev &M, const ModelF32 &F, const ParamsDev &P,
+                                          uint64_t start, int cnt, double thr, float *tf)
+{
+    constexpr int RS = rec_stride<TTC>();
     for (int j = threadIdx.x & 31; j < cnt; j += 32) {
         const uint64_t i = start + j;
+        float *rc = tf + j * RS;
+        float *cp = rc + R_C0;
         double f[AEB_NFIELDS];
         load_fields(P, i, f);
         int kind = K_RUN, nd = 0;
         if (!sample_valid(f)) {
             kind = K_INVALID;
         } else {
-            nd = steps_to_reach_dev(f[kTdelay], M.dt);
+            nd = steps_to_reach_f32(f[kTdelay], M.dt, F.idt);
             if (LEAD && f[kD0] <= 0.0) kind = K_CONTACT0;
             else if (f[kV0] <= 0.0) kind = K_STOP0;
             else if (M.n_max == 0) kind = K_HORIZON0;
         }
-        ti[R_NDELAY * T + j] = nd;
-        ti[R_KIND * T + j] = kind;
+        cp[C_NDELAY] = __int_as_float(nd);
+        rc[R_KIND] = __int_as_float(kind);
         if (kind != K_RUN) continue;
         // speed scale s = sqrt(k), bounded below so that a drag-free sample
         // keeps its scaled state in the normal binary32 range.  The constants
@@ -172,69 +198,81 @@ __device__ __forceinline__ void prep_tile(const ModelDev &M, const ModelF32 &F, 
         const float sc = fmaxf(sqrtf(k32), 1e-18f);
         const double sd = (double)sc;
         const float nh6s = __double2float_rn(-(sd * M.h6));
-        const double sigma = (sd * sd) / -(double)nh6s;  // gap scale s / h6
+        // gap scale sigma = s^2 / (-nh6s) = s / h6: 1 / (-nh6s) from the
+        // binary32 reciprocal and one binary64 Newton step (relative error
+        // ~4e-15, where a binary64 division would be slow)
+        const double x6 = -(double)nh6s;
+        const double r0 = (double)__frcp_rn(-nh6s);
+        const double r6 = fma(r0, fma(-x6, r0, 1.0), r0);
+        const double sigma = (sd * sd) * r6;
         const double w0 = sd * f[kV0], g0 = sigma * f[kD0];
         const float w0h = __double2float_rn(w0), g0h = __double2float_rn(g0);
-        tf[R_W0H * T + j] = w0h;
-        tf[R_W0L * T + j] = __double2float_rn(w0 - (double)w0h);
-        tf[R_G0H * T + j] = g0h;
-        tf[R_G0L * T + j] = __double2float_rn(g0 - (double)g0h);
-        tf[R_GS * T + j] = __double2float_rn(f[kGs]);
-        tf[R_S * T + j] = sc;
-        tf[R_NH2S * T + j] = __double2float_rn(-(sd * M.h2));
-        tf[R_NH6S * T + j] = nh6s;
-        tf[R_SIGMA * T + j] = __double2float_rn(sigma);
+        rc[R_W0H] = w0h;
+        rc[R_W0L] = __double2float_rn(w0 - (double)w0h);
+        rc[R_G0H] = g0h;
+        rc[R_G0L] = __double2float_rn(g0 - (double)g0h);
+        rc[R_NH2S] = __double2float_rn(-(sd * M.h2));
+        rc[R_NH6S] = nh6s;
+        cp[C_GS] = __double2float_rn(f[kGs]);
+        cp[C_S] = sc;
+        cp[C_SIGMA] = __double2float_rn(sigma);
         const float mu = __double2float_rn(f[kMu]), mh = mu * F.hl;
         if (M.cap_mode == AEB_CAP_LUMPED) {
-            tf[R_F0 * T + j] = finf();
-            tf[R_F1 * T + j] = 0.0f;
-            tf[R_R0 * T + j] = finf();
-            tf[R_R1 * T + j] = 0.0f;
-            tf[R_MG * T + j] = (mu * F.g) / (1.0f + mh);
+            cp[C_F0] = finf();
+            cp[C_F1] = 0.0f;
+            cp[C_R0] = finf();
+            cp[C_R1] = 0.0f;
+            cp[C_MG] = (mu * F.g) / (1.0f + mh);
         } else {
             const float mg = mu * __double2float_rn(f[kGc]);
             const float im = 1.0f / (1.0f - mh), ip = 1.0f / (1.0f + mh);
-            tf[R_F0 * T + j] = (mg * F.phi_f) * im;
-            tf[R_F1 * T + j] = (1.0f - F.beta) * im;
-            tf[R_R0 * T + j] = (mg * (1.0f - F.phi_f)) * ip;
-            tf[R_R1 * T + j] = F.beta * ip;
-            tf[R_MG * T + j] = mg;
+            cp[C_F0] = (mg * F.phi_f) * im;
+            cp[C_F1] = (1.0f - F.beta) * im;
+            cp[C_R0] = (mg * (1.0f - F.phi_f)) * ip;
+            cp[C_R1] = F.beta * ip;
+            cp[C_MG] = mg;
         }
         float nmp = -1.0f;
         if (f[kTau] > 0.0) {
             const float z = F.dt / __double2float_rn(f[kTau]);
-            tf[R_NP2 * T + j] = -(1.0f - 0.5f * z);
-            tf[R_NP3 * T + j] = -(1.0f - 0.5f * z + 0.25f * z * z);
-            tf[R_NP4 * T + j] = -(1.0f - z + 0.5f * z * z - 0.25f * z * z * z);
+            cp[C_NP2] = -(1.0f - 0.5f * z);
+            cp[C_NP3] = -(1.0f - 0.5f * z + 0.25f * z * z);
+            cp[C_NP4] = -(1.0f - z + 0.5f * z * z - 0.25f * z * z * z);
             nmp = -(z * (1.0f + z * (-0.5f + z * (1.0f / 6.0f - z / 24.0f))));
         } else {
-            tf[R_NP2 * T + j] = 0.0f;
-            tf[R_NP3 * T + j] = 0.0f;
-            tf[R_NP4 * T + j] = 0.0f;
+            cp[C_NP2] = 0.0f;
+            cp[C_NP3] = 0.0f;
+            cp[C_NP4] = 0.0f;
         }
-        tf[R_NMP * T + j] = nmp;
+        rc[R_NMP] = nmp;
         if (TTC) {  // (g + noise) - thr v scaled by sigma: G + sigma noise - (sigma thr / s) w
-            const double ts = thr * (sigma / sd);
+            const double ts = thr * (sd * r6);  // sigma / s
             const float tsh = __double2float_rn(ts);
-            tf[R_NZ * T + j] = __double2float_rn(sigma * f[kNoise]);
-            tf[R_THRH * T + j] = tsh;
-            tf[R_THRL * T + j] = __double2float_rn(ts - (double)tsh);
+            cp[C_NZ] = __double2float_rn(sigma * f[kNoise]);
+            cp[C_THRH] = tsh;
+            cp[C_THRL] = __double2float_rn(ts - (double)tsh);
         }
     }
 }
 
 // Per-lane values read only on rare paths (piece changes, slow steps, the TTC
-// test, records) live in a column of the warp's shared slab, field-major with
-// stride 32, to keep the step loop's register budget small.
+// test, records) live in a column of the warp's shared slab, to keep the step
+// loop's register budget small: the lane's own fields, its rows, then the
+// record block C_* (both written by the whole warp at refill).  Lane-major
+// with an odd stride, so that 32 lanes reading one field, or 32 lanes writing
+// one lane's column, hit 32 different banks.
 enum {
-    L_F0, L_F1, L_R0, L_R1, L_MG, L_GS, L_U, L_S, L_ETHK, L_NP1, L_NP2, L_NP3, L_NP4,  // floats
-    L_SIGMA, L_QF,
-    L_NB, L_NDELAY, L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI, L_KIDXLO, L_KIDXHI,         // ints
-    L_NW_BASE,
-    L_NZ = L_NW_BASE, L_THRH, L_THRL, L_NCHK, L_NW_TTC  // TTC trigger only (NCHK: int)
+    L_U, L_ETHK, L_NB, L_NCHK, L_NP1, L_QF,                       // the lane's (NCHK: TTC)
+    L_PIDXLO, L_PIDXHI, L_IDXLO, L_IDXHI, L_KIDXLO, L_KIDXHI,     // rows (two words each)
+    L_C0,                                                         // the record block
+    L_NDELAY = L_C0 + C_NDELAY, L_GS = L_C0 + C_GS, L_S = L_C0 + C_S,
+    L_SIGMA = L_C0 + C_SIGMA, L_F0 = L_C0 + C_F0, L_F1 = L_C0 + C_F1, L_R0 = L_C0 + C_R0,
+    L_R1 = L_C0 + C_R1, L_MG = L_C0 + C_MG, L_NP2 = L_C0 + C_NP2, L_NP3 = L_C0 + C_NP3,
+    L_NP4 = L_C0 + C_NP4, L_NZ = L_C0 + C_NZ, L_THRH = L_C0 + C_THRH, L_THRL = L_C0 + C_THRL
 };
 template <bool TTC>
-__host__ __device__ constexpr int cold_fields() { return TTC ? L_NW_TTC : L_NW_BASE; }
+__host__ __device__ constexpr int cold_stride() { return (L_C0 + copy_fields<TTC>()) | 1; }
+static_assert(L_C0 - L_PIDXLO + C_NTTC <= 32, "a column's rows and record block fit one warp");
 
 template <int LEAD, bool TTC, bool PERC>
 struct Lane32 {
@@ -246,12 +284,13 @@ struct Lane32 {
     float nmP;
     int32_t n, ev;                // step, next slow step
     bool trig;
-    float *cold;                  // this lane's column: cold[field * 32]
+    float *cold;                  // this lane's column: cold[field]
 
-    __device__ __forceinline__ float cf(int f) const { return cold[f * 32]; }
-    __device__ __forceinline__ void set_cf(int f, float x) { cold[f * 32] = x; }
-    __device__ __forceinline__ int ci(int f) const { return __float_as_int(cold[f * 32]); }
-    __device__ __forceinline__ void set_ci(int f, int x) { cold[f * 32] = __int_as_float(x); }
+    __device__ __forceinline__ float cf(int f) const { return cold[f]; }
+    __device__ __forceinline__ void set_cf(int f, float x) { cold[f] = x; }
+    __device__ __forceinline__ int ci(int f) const { return __float_as_int(cold[f]); }
+    __device__ __forceinline__ void set_ci(int f, int x) { cold[f] = __int_as_float(x); }
+    __device__ __forceinline__ float np1() const { return cf(L_NP1); }  // -p1
     __device__ __forceinline__ uint64_t pidx() const
     {
         return (uint64_t)(uint32_t)ci(L_PIDXLO) | ((uint64_t)(uint32_t)ci(L_PIDXHI) << 32);
@@ -283,7 +322,7 @@ struct Lane32 {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (b_[j] < bb && a_[j] < finf()) B = fminf(B, __fdividef(a_[j] - ab, bb - b_[j]));
-        a1 = bb * cf(L_NP1);
+        a1 = bb * np1();
         a2 = bb * cf(L_NP2);
         a3 = bb * cf(L_NP3);
         a4 = bb * cf(L_NP4);
@@ -352,7 +391,7 @@ struct Lane32 {
         // rounding as fmaf) cost two issue slots instead of four
         float2 X12, X34;
         if (FULL_MIN) {
-            X12 = make_float2(rg_full(cf(L_NP1)), rg_full(cf(L_NP2)));
+            X12 = make_float2(rg_full(np1()), rg_full(cf(L_NP2)));
             X34 = make_float2(rg_full(cf(L_NP3)), rg_full(cf(L_NP4)));
         } else {
             const float2 ee = make_float2(e, e), cc = make_float2(C, C);
@@ -543,7 +582,7 @@ struct Lane32 {
     {
         set_cf(L_U, F.acmd);
         e = e - F.acmd;
-        set_piece(-fmaf(-cf(L_NP1), e, F.acmd));
+        set_piece(-fmaf(-np1(), e, F.acmd));
         ev = n_last;
     }
 
@@ -563,7 +602,7 @@ struct Lane32 {
         if (!ended) {
             commit(vl1, gl1, en);
             normalize();
-            set_piece(-fmaf(-cf(L_NP1), e, cf(L_U)));
+            set_piece(-fmaf(-np1(), e, cf(L_U)));
             next_event(n_last);
         }
         return ended;
@@ -775,14 +814,14 @@ struct Lane32 {
         n = n0;
     }
 
-    // Load sample `slot` of the warp's tile (parameter row pi, output row i);
-    // true if it ended at once (stored).
+    // Take the prepared record rc (parameter row pi, output row i); true if
+    // the sample ended at once (stored).  The record block and the rows reach
+    // the lane's column from the whole warp afterwards (copy_records).
     __device__ __forceinline__ bool init(const ModelDev &M, const ParamsDev &P, const OutDev &O,
-                                         uint64_t pi, uint64_t i, uint64_t ki, int slot, int T,
-                                         const float *tf, const int *ti)
+                                         uint64_t pi, uint64_t i, const float *rc)
     {
-        const int kind = ti[R_KIND * T + slot];
-        const int32_t n_delay = ti[R_NDELAY * T + slot];
+        const int kind = __float_as_int(rc[R_KIND]);
+        const int32_t n_delay = __float_as_int(rc[R_C0 + C_NDELAY]);
         if (kind != K_RUN) {
             const int32_t on = TTC ? -1 : n_delay;
             if (kind == K_INVALID) {
@@ -797,42 +836,19 @@ struct Lane32 {
             }
             return true;
         }
-        vh = tf[R_W0H * T + slot];
-        vl = tf[R_W0L * T + slot];
-        gh = tf[R_G0H * T + slot];
-        gl = tf[R_G0L * T + slot];
-        nh2s = tf[R_NH2S * T + slot];
+        vh = rc[R_W0H];
+        vl = rc[R_W0L];
+        gh = rc[R_G0H];
+        gl = rc[R_G0L];
+        nh2s = rc[R_NH2S];
         ndts = 2.0f * nh2s;
-        nh6s = tf[R_NH6S * T + slot];
-        // np1 = -1 when tau > 0 (then np2 or np3 is nonzero), else 0
-        set_cf(L_NP1, (tf[R_NP2 * T + slot] != 0.0f || tf[R_NP3 * T + slot] != 0.0f) ? -1.0f : 0.0f);
-        set_cf(L_NP2, tf[R_NP2 * T + slot]);
-        set_cf(L_NP3, tf[R_NP3 * T + slot]);
-        set_cf(L_NP4, tf[R_NP4 * T + slot]);
-        nmP = tf[R_NMP * T + slot];
-        set_cf(L_GS, tf[R_GS * T + slot]);
-        set_cf(L_F0, tf[R_F0 * T + slot]);
-        set_cf(L_F1, tf[R_F1 * T + slot]);
-        set_cf(L_R0, tf[R_R0 * T + slot]);
-        set_cf(L_R1, tf[R_R1 * T + slot]);
-        set_cf(L_MG, tf[R_MG * T + slot]);
-        set_cf(L_S, tf[R_S * T + slot]);
-        set_cf(L_SIGMA, tf[R_SIGMA * T + slot]);
+        nh6s = rc[R_NH6S];
+        nmP = rc[R_NMP];
+        // -p1 = -1 when tau > 0 (then np2 or np3 is nonzero), else 0
+        set_cf(L_NP1, (rc[R_C0 + C_NP2] != 0.0f || rc[R_C0 + C_NP3] != 0.0f) ? -1.0f : 0.0f);
         // (1 - mP)^(K-1): the actuator decay over a window's last K-1 steps
         set_cf(L_QF, powi<AEB_FP32_WINDOW - 1>(1.0f + nmP));
-        set_ci(L_NDELAY, n_delay);
-        set_ci(L_PIDXLO, (int)(uint32_t)pi);
-        set_ci(L_PIDXHI, (int)(uint32_t)(pi >> 32));
-        set_ci(L_IDXLO, (int)(uint32_t)i);
-        set_ci(L_IDXHI, (int)(uint32_t)(i >> 32));
-        set_ci(L_KIDXLO, (int)(uint32_t)ki);
-        set_ci(L_KIDXHI, (int)(uint32_t)(ki >> 32));
-        if (TTC) {
-            set_cf(L_NZ, tf[R_NZ * T + slot]);
-            set_ci(L_NCHK, 0);  // test the trigger at the first step
-            set_cf(L_THRH, tf[R_THRH * T + slot]);
-            set_cf(L_THRL, tf[R_THRL * T + slot]);
-        }
+        if (TTC) set_ci(L_NCHK, 0);  // test the trigger at the first step
         e = 0.0f;  // a = 0 and the command is 0 before onset
         set_cf(L_U, 0.0f);
         n = 0;
@@ -843,13 +859,42 @@ struct Lane32 {
         // realised deceleration min(D, f0 + f1 D, r0 + r1 D, mu g cos) is 0
         // (mu >= 0): the stage term r + g sin(theta) is g sin(theta), and no
         // breakpoint can be reached.  The piece is selected at onset.
-        C = cf(L_GS);
+        C = rc[R_C0 + C_GS];
         a1 = a2 = a3 = a4 = 0.0f;
         eth = -finf();
         set_cf(L_ETHK, -finf());
         return false;
     }
 };
+
+// After lanes took samples cursor, cursor + 1, ... of the tile (the lanes of
+// `taken`, in lane order): the rows and the record block of those in `keep`
+// reach their columns, written by the whole warp (lane t: word t of the
+// column's rows-and-record part; consecutive words, so no bank conflicts),
+// instead of ~20 loads and stores by each refilling lane alone.
+template <bool TTC>
+__device__ __forceinline__ void copy_records(float *coldw, const float *tf, const Tile &tile,
+                                             int cursor, unsigned taken, unsigned keep)
+{
+    constexpr int NC = copy_fields<TTC>(), CS = cold_stride<TTC>(), RS = rec_stride<TTC>();
+    const int t = (int)(threadIdx.x & 31u);
+    const uint64_t base = t < 2 ? tile.p0 : t < 4 ? tile.o0 : tile.k0;  // rows (t < 6)
+    int r = 0;
+    for (unsigned tk = taken; tk; tk &= tk - 1, ++r) {
+        const int l = __ffs(tk) - 1;
+        if (!((keep >> l) & 1u)) continue;
+        const int slot = cursor + r;
+        float w = 0.0f;
+        if (t < L_C0 - L_PIDXLO) {
+            const uint64_t v = base + (uint64_t)slot;
+            w = __int_as_float((int)(uint32_t)((t & 1) ? (v >> 32) : v));
+        } else if (t < L_C0 - L_PIDXLO + NC) {
+            w = tf[slot * RS + R_C0 + (t - (L_C0 - L_PIDXLO))];
+        }
+        if (t < L_C0 - L_PIDXLO + NC) coldw[l * CS + L_PIDXLO + t] = w;
+    }
+    __syncwarp();  // the columns are read by their lanes from here on
+}
 
 // Records of ended rollouts waiting for the warp's flush, per warp,
 // field-major.  A window record (len > 0) holds the state at the start of the
@@ -877,7 +922,7 @@ constexpr int kBandState = 2 * AEB_FP32_WINDOW + 4;
 template <bool TTC, bool PERC>
 __host__ __device__ constexpr int warp_words(int T)
 {
-    return (rec_floats<TTC>() + R_NI) * T + kBatchWords + cold_fields<TTC>() * 32 +
+    return rec_stride<TTC>() * T + kBatchWords + cold_stride<TTC>() * 32 +
            (PERC ? kBandSlots * (kBandCache + G_NI + kBandState) : 0);
 }
 template <bool TTC, bool PERC>
@@ -1006,11 +1051,10 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     const unsigned lane = threadIdx.x & 31u;
     const int T = (int)W.tile;
     float *tf = smem + (threadIdx.x >> 5) * warp_words<TTC, PERC>(T);
-    int *ti = reinterpret_cast<int *>(tf + rec_floats<TTC>() * T);
-    float *bf = tf + (rec_floats<TTC>() + R_NI) * T;
+    float *bf = tf + rec_stride<TTC>() * T;
     int *bi = reinterpret_cast<int *>(bf + B_NF * 32);
     float *coldw = bf + kBatchWords;
-    float *rdg = coldw + cold_fields<TTC>() * 32;  // band readings (per-step perception)
+    float *rdg = coldw + cold_stride<TTC>() * 32;  // band readings (per-step perception)
     int *btag = reinterpret_cast<int *>(rdg + kBandSlots * kBandCache);
     float *sst = reinterpret_cast<float *>(btag + kBandSlots * G_NI);  // band window states
     if (PERC && (int)lane < kBandSlots) btag[lane * G_NI + G_CNT] = 0;  // nothing cached
@@ -1028,7 +1072,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
     int cursor = 0, bcount = 0;
     bool dry = false;
     Lane32<LEAD, TTC, PERC> L;
-    L.cold = coldw + lane;
+    L.cold = coldw + lane * cold_stride<TTC>();
     bool active = false;
     unsigned need = kFull;
     for (;;) {
@@ -1047,7 +1091,7 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                     tile = nt;
                     cursor = 0;
                     __syncwarp();  // every lane has read its record of the previous tile
-                    prep_tile<LEAD, TTC>(M, F, P, tile.p0, tile.count, tile.thr, T, tf, ti);
+                    prep_tile<LEAD, TTC>(M, F, P, tile.p0, tile.count, tile.thr, tf);
                     __syncwarp();
                 }
                 const unsigned rank = __popc(need & lanemask_lt());
@@ -1056,12 +1100,14 @@ k_rollout_fp32(ModelDev M, ModelF32 F, ParamsDev P, OutDev O, WorkDev W)
                 if (got) {
                     const int slot = cursor + (int)rank;
                     active = true;
-                    ended = L.init(M, P, O, tile.p0 + slot, tile.o0 + slot, tile.k0 + slot, slot,
-                                   T, tf, ti);
+                    ended = L.init(M, P, O, tile.p0 + slot, tile.o0 + slot,
+                                   tf + slot * rec_stride<TTC>());
                 }
                 const unsigned taken = __ballot_sync(kFull, got);
+                const unsigned endm = __ballot_sync(kFull, ended);
+                copy_records<TTC>(coldw, tf, tile, cursor, taken, taken & ~endm);
                 cursor += __popc(taken);
-                need = (need & ~taken) | __ballot_sync(kFull, ended);
+                need = (need & ~taken) | endm;
             }
             if (!__any_sync(kFull, active)) {
                 flush_batch<LEAD, TTC, PERC>(M, F, P, O, bf, bi, bcount);
@@ -1309,6 +1355,7 @@ ModelF32 to_f32(const ModelDev &m)
     f.phi_f = (float)m.phi_f;
     f.beta = (float)m.beta;
     f.dt = (float)m.dt;
+    f.idt = (float)(1.0 / m.dt);
     f.lv0 = (float)m.lead_v0;
     f.lb = (float)m.lead_decel;
     f.lhb = (float)(0.5 * m.lead_decel);
