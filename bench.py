@@ -54,12 +54,12 @@ SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 FP64_PEAK_TFLOPS = 1.25  # GB300 dense FP64, nominal
 # DRAM bytes per sample of the FP32 rollout kernel, from one ncu capture at
-# N = 2e6 (184.1 MB per launch); traffic grows in proportion to the samples.
-FP32_TRAFFIC_BYTES_PER_SAMPLE = 184.10752e6 / 2e6
+# N = 2e6 (199.7 MB per launch); traffic grows in proportion to the samples.
+FP32_TRAFFIC_BYTES_PER_SAMPLE = 199.657728e6 / 2e6
 # thread instructions the FP32 kernel executes per RK4 lane-step on this
 # workload (ncu smsp__inst_executed x thread_inst_executed_per_inst_executed at
 # N = 2e6, same profile); the issue-slot view of the roofline
-FP32_THREAD_INST_PER_STEP = 22.15
+FP32_THREAD_INST_PER_STEP = 22.46
 FP32_ISSUE_PEAK = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6  # lane-instructions/s
 
 
