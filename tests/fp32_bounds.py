@@ -105,8 +105,9 @@ def fp32_report(m, got, exp, ties=(0, 0.0)):
         dv = np.abs(got["v_imp"][ct] - vi)
         dtc = np.abs(got["t_end"][ct] - exp["t_end"][ct])
         rep["v_imp_abs_max"] = float(dv.max())
-        rep["contact_dt_x_v_over_d0_max"] = float((dtc * vi / d0).max())
-        rep["contact_dv_x_v_over_d0_max"] = float((dv * vi / d0).max())
+        d0r = np.maximum(d0, 1e-3)  # (report only: a contact at x = 0 has no ratio)
+        rep["contact_dt_x_v_over_d0_max"] = float((dtc * vi / d0r).max())
+        rep["contact_dv_x_v_over_d0_max"] = float((dv * vi / d0r).max())
         assert np.all(dtc * vi <= 1e-5 * d0), rep
         assert np.all(dv * vi <= R_MAX * 1e-5 * d0), rep
     sp = same & (s64 == 0)

@@ -227,6 +227,47 @@ def test_fp32_comp_within_tolerance(aeb, oracle_mod, name):
     assert rep["onset_ties"] <= max(3, 1e-3 * n), rep
 
 
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 257, 1031, 4099])
+def test_fp32_ragged_sizes(aeb, oracle_mod, n):
+    """Sizes that leave the last warp tile partial, with the edge samples
+    (invalid, already stopped or in contact, no drag, tau = 0) placed at the
+    end, so that samples that end at once sit inside partial tiles; the TTC
+    trigger variant too."""
+    for m in (ai.single_model(), ai.ttc_model(thr=2.0)):
+        p = ai.concat_params([ai.draw_params(m, ai.single_scenario(seed=30 + n), n),
+                              ai.edge_params(m)])
+        k = len(p["v0"])
+        exp = oracle_mod.rollout(m, p, threads=8)
+        got = gpu_rollout(aeb, m, p, aeb.FP32_COMP)
+        exp, ties = resolve_onset_ties(oracle_mod, m, p, np.arange(k), got, exp)
+        inv = exp["status"] == 255
+        assert np.array_equal(got["status"][inv], exp["status"][inv])
+        assert np.all(np.isnan(got["x_ref"][inv])) and np.all(got["n_steps"][inv] == 0)
+        ok = ~inv
+        g, e = with_gap(got, p, m), with_gap(exp, p, m)
+        fp32_report(m, {c: v[ok] for c, v in g.items()}, {c: v[ok] for c, v in e.items()}, ties)
+
+
+def test_fp32_every_tile_size_same_results(aeb):
+    """Per-sample results do not depend on the tile a warp prepares (32 ... 256
+    samples, the largest allowed) nor on the resident blocks per SM: a lane's
+    windows depend on its own state only."""
+    m = ai.single_model()
+    p = ai.concat_params([ai.draw_params(m, ai.single_scenario(seed=31), 70_001),
+                          ai.edge_params(m)])
+    old = aeb.aeb_get_launch_config(aeb.FP32_COMP)
+    try:
+        aeb.aeb_set_launch_config(aeb.FP32_COMP, 32, 6)
+        ref = gpu_rollout(aeb, m, p, aeb.FP32_COMP)
+        for tile, bps in ((64, 6), (128, 4), (256, 2), (32, 3)):
+            aeb.aeb_set_launch_config(aeb.FP32_COMP, tile, bps)
+            got = gpu_rollout(aeb, m, p, aeb.FP32_COMP)
+            for k in ref:
+                assert bits_equal(got[k], ref[k]), (tile, bps, k)
+    finally:
+        aeb.aeb_set_launch_config(aeb.FP32_COMP, old.tile, old.blocks_per_sm)
+
+
 def test_reduce_against_oracle(aeb, oracle_mod):
     m = ai.single_model()
     p = ai.concat_params([ai.draw_params(m, ai.single_scenario(seed=20), 12_345),
