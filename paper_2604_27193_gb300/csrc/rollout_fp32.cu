@@ -43,7 +43,8 @@
 // shared memory (brake-onset step by the binary64 rule, hi/lo splits of the
 // scaled v0 and d0, scaled step factors, cap coefficients, actuator
 // multipliers, the scaled TTC threshold and range noise).  Lanes whose rollout
-// ends refill from that tile.  The binary64 refinement of the last step (linear
+// ends refill from that tile (the whole warp copies their records' rarely read
+// part into their shared-memory columns).  The binary64 refinement of the last step (linear
 // stop/contact interpolation from the hi + lo pairs) is also batched: an ending
 // lane queues its terminal state in the warp's shared slab, and the warp refines
 // 32 queued rollouts at once.
