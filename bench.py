@@ -737,9 +737,20 @@ def main():
         aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
+    # the box's pinned host-to-device copy rate (outside the timed region): the
+    # e2e figure hides the uploads behind the rollouts only while they are fast
+    # enough (growing chunks, each uploaded during the previous one's rollouts)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for f in ai.FIELDS:
+        P[f].copy_(host[f], non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 8 * len(ai.FIELDS) * N / (c0.elapsed_time(c1) / 1e3) / 1e9
     e2e = {"value": world * N * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 8 * len(ai.FIELDS) * N, "d2h_bytes_per_step": aeb.STATS_BYTES,
-           "api": "aeb_evaluate (pinned host params -> host stats)"}
+           "api": "aeb_evaluate (pinned host params -> host stats)",
+           "h2d_copy_gbs": h2d_gbs}
     # the same, from the seed: host sampling (all host threads) inside the
     # step, each chunk drawn while the previous one uploads and rolls out
     t1 = time.perf_counter()
