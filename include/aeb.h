@@ -436,10 +436,14 @@ aeb_status aeb_reduce_noalloc(const aeb_outputs *out, uint64_t n, const aeb_hist
  *   host_stats  host aeb_stats written on success
  *   host_out    host columns for per-sample outputs, or NULL / NULL members
  * Above 2^19 samples the upload is cut into chunks of growing length (2^18
- * samples first, then twice the previous one), each rolled out as soon as
- * it has arrived, on internal streams ordered after the work already queued
- * on `stream`; results are the same bits as one aeb_rollout + aeb_reduce of
- * all n samples (sample i keeps row i for its perception readings).
+ * samples first, then each a factor g longer than the one before), each
+ * rolled out as soon as it has arrived, on internal streams ordered after the
+ * work already queued on `stream`.  g is 2 on the first call on a stream;
+ * each call times its uploads and its first chunk's rollouts and sets g for
+ * the next call on that stream (within [1.25, 4]), so that a chunk's upload
+ * ends before the previous chunk's rollouts on this machine's copy rate.
+ * Results are the same bits as one aeb_rollout + aeb_reduce of all n samples
+ * (sample i keeps row i for its perception readings), whatever the chunks.
  * The device buffers, internal streams and events are kept per (device,
  * stream) and grown as needed until the process exits; calls on the same
  * stream from several threads must be serialised by the caller.

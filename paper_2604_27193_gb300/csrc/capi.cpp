@@ -1,6 +1,8 @@
 // capi.cpp -- the C ABI entry points other than sampling: argument checks,
 // conversion of the model to the kernels' form, library scratch, dispatch.
+#include <algorithm>
 #include <cmath>
+#include <initializer_list>
 #include <cstdint>
 #include <cstring>
 #include <limits>
@@ -238,10 +240,16 @@ aeb_status reduce_impl(const aeb_outputs *out, uint64_t n, const aeb_hist_spec &
 // rollouts do: an upload moves 80 B per sample (~1.3 ns per sample at the
 // pinned-host copy rate measured on GB300) against ~2.7 ns per sample of
 // FP32 rollout, so a chunk may be at most about twice the one before (six
-// times left the GPU waiting for the last chunk's copy).
+// times left the GPU waiting for the last chunk's copy).  The host-to-device
+// copy rate differs between machines (60-200 GB/s measured on GB300 machines), so
+// each call times its own uploads and its first chunk's rollouts (the first
+// chunk runs alone) and sets the growth of the next call on that stream to
+// 0.8 x (rollout time per sample) / (upload time per sample), within
+// [kEvalGrowMin, kEvalGrowMax]; the first call grows by 2.  Results do not
+// depend on the chunks.
 constexpr int kEvalMaxChunks = 12;
 constexpr uint64_t kEvalFirstChunk = uint64_t(1) << 18;
-constexpr uint64_t kEvalGrow = 2;
+constexpr double kEvalGrowFirst = 2.0, kEvalGrowMin = 1.25, kEvalGrowMax = 4.0;
 // aeb_evaluate_scenario draws chunks of kSampledChunk samples on the host into
 // two pinned staging buffers (pin[k % 2]); the upload of chunk k records
 // uploaded[k % 2], after which the host may draw chunk k + 2 into that buffer.
@@ -253,6 +261,10 @@ struct EvalBuffers {
     cudaEvent_t start = nullptr, copied[kEvalMaxChunks] = {}, done[2] = {nullptr, nullptr};
     double *pin[2] = {nullptr, nullptr};  // AEB_NFIELDS columns of kSampledChunk each
     cudaEvent_t uploaded[2] = {nullptr, nullptr};
+    // timing of the last aeb_evaluate on this stream: every upload (up0 .. up1)
+    // and the first chunk's rollouts (run0 .. run1); the next call's growth
+    cudaEvent_t up0 = nullptr, up1 = nullptr, run0 = nullptr, run1 = nullptr;
+    double grow = kEvalGrowFirst;
 };
 
 cudaError_t eval_streams(EvalBuffers &b)
@@ -268,6 +280,8 @@ cudaError_t eval_streams(EvalBuffers &b)
         e = cudaEventCreateWithFlags(&b.done[i], cudaEventDisableTiming);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&b.uploaded[i], cudaEventDisableTiming);
+    for (cudaEvent_t *t : {&b.up0, &b.up1, &b.run0, &b.run1})
+        if (e == cudaSuccess) e = cudaEventCreate(t);
     return e;
 }
 std::map<std::pair<int, uintptr_t>, EvalBuffers> g_eval;
@@ -451,6 +465,7 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
 
     ParamsDev pd;
     check_params(&dp, &pd);
+    uint64_t timed_first = 0;  // samples of the timed first chunk (0: not timed)
     if (n > 0) {
         aeb_outputs want = dout;
         if (!host_out || !host_out->x_raw) want.x_raw = nullptr;
@@ -462,8 +477,8 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
         // to 2 kEvalFirstChunk samples)
         uint64_t bound[kEvalMaxChunks + 1] = {0};
         int chunks = 0;
-        for (uint64_t len = kEvalFirstChunk; bound[chunks] < n; len *= kEvalGrow) {
-            const uint64_t rest = n - bound[chunks];
+        for (double lenf = (double)kEvalFirstChunk; bound[chunks] < n; lenf *= eb->grow) {
+            const uint64_t len = (uint64_t)lenf, rest = n - bound[chunks];
             const bool last = chunks == kEvalMaxChunks - 1 || rest <= len ||
                               (chunks == 0 && rest <= 2 * kEvalFirstChunk);
             bound[chunks + 1] = bound[chunks] + (last ? rest : len);
@@ -472,6 +487,7 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
         // the copies start after the work already queued on the caller's stream
         e = cudaEventRecord(eb->start, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(eb->copy, eb->start, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(eb->up0, eb->copy);
         if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: stream order");
         for (int k = 0; k < chunks; ++k) {
             const uint64_t off = bound[k], len = bound[k + 1] - bound[k];
@@ -484,11 +500,18 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
             }
             cudaStream_t cs = eb->comp[k % 2];
             e = cudaEventRecord(eb->copied[k], eb->copy);
+            if (e == cudaSuccess && k == chunks - 1) e = cudaEventRecord(eb->up1, eb->copy);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, eb->copied[k], 0);
+            if (e == cudaSuccess && k == 0) e = cudaEventRecord(eb->run0, cs);
             if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: chunk order");
             st = rollout_impl(md, pk, len, precision, offset_out(od, off), cs, off);
             if (st != AEB_OK) return st;
+            if (k == 0) {
+                e = cudaEventRecord(eb->run1, cs);
+                if (e != cudaSuccess) return cuda_fail(e, "aeb_evaluate: chunk timing");
+            }
         }
+        timed_first = chunks > 1 ? bound[1] : 0;
         for (int i = 0; i < 2; ++i) {
             e = cudaEventRecord(eb->done[i], eb->comp[i]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, eb->done[i], 0);
@@ -516,6 +539,16 @@ extern "C" aeb_status aeb_evaluate(const aeb_model *model, const aeb_params *par
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (timed_first > 0) {  // the next call's chunk growth (see EvalBuffers)
+        float up_ms = 0.0f, run_ms = 0.0f;
+        if (cudaEventElapsedTime(&up_ms, eb->up0, eb->up1) == cudaSuccess &&
+            cudaEventElapsedTime(&run_ms, eb->run0, eb->run1) == cudaSuccess && up_ms > 0.0f &&
+            run_ms > 0.0f) {
+            const double g = 0.8 * ((double)run_ms / (double)timed_first) /
+                             ((double)up_ms / (double)n);
+            eb->grow = std::min(kEvalGrowMax, std::max(kEvalGrowMin, g));
+        }
+    }
     return AEB_OK;
 }
 
