@@ -690,6 +690,31 @@ def main():
     value = world * N * args.steps / (ms_total / 1e3)
     achieved = steps_per_launch * FLOPS_PER_STEP / (roll_ms / 1e3) / 1e12
 
+    # ---- end to end through the public host-buffer call ------------------
+    # (right after the headline, before the binary64 arm's seconds at full power)
+    aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)  # sizes the buffers
+    barrier()
+    e2e_steps = max(2, min(args.steps, 5))
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+    # the box's pinned host-to-device copy rate (outside the timed region): the
+    # e2e figure hides the uploads behind the rollouts only while they are fast
+    # enough (growing chunks, each uploaded during the previous one's rollouts)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for f in ai.FIELDS:
+        P[f].copy_(host[f], non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 8 * len(ai.FIELDS) * N / (c0.elapsed_time(c1) / 1e3) / 1e9
+    e2e = {"value": world * N * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * len(ai.FIELDS) * N, "d2h_bytes_per_step": aeb.STATS_BYTES,
+           "api": "aeb_evaluate (pinned host params -> host stats)",
+           "h2d_copy_gbs": h2d_gbs, "clocks": clk_e2e.summary()}
     # ---- FP64 plain on the same samples ----------------------------------
     pooled = pooled_stats(aeb, torch, dist, S, world, dev)
     fp64 = None
@@ -728,29 +753,6 @@ def main():
                         "add/multiply rate (measured_pipe_peaks.fp64_add_tops)",
                 "fp32_error": err}
 
-    # ---- end to end through the public host-buffer call ------------------
-    aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)  # sizes the buffers
-    barrier()
-    e2e_steps = max(2, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        aeb.aeb_evaluate(m, host, N, aeb.FP32_COMP, hist, stream=stream)
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    # the box's pinned host-to-device copy rate (outside the timed region): the
-    # e2e figure hides the uploads behind the rollouts only while they are fast
-    # enough (growing chunks, each uploaded during the previous one's rollouts)
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    for f in ai.FIELDS:
-        P[f].copy_(host[f], non_blocking=True)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    h2d_gbs = 8 * len(ai.FIELDS) * N / (c0.elapsed_time(c1) / 1e3) / 1e9
-    e2e = {"value": world * N * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 8 * len(ai.FIELDS) * N, "d2h_bytes_per_step": aeb.STATS_BYTES,
-           "api": "aeb_evaluate (pinned host params -> host stats)",
-           "h2d_copy_gbs": h2d_gbs}
     # the same, from the seed: host sampling (all host threads) inside the
     # step, each chunk drawn while the previous one uploads and rolls out
     t1 = time.perf_counter()
