@@ -357,6 +357,29 @@ def test_evaluate_chunked_upload(aeb, n):
     assert bytes(st) == bytes(S.cpu().numpy())
 
 
+def test_evaluate_adaptive_chunks_same_bits(aeb):
+    """From its second call on a stream, aeb_evaluate grows its chunks by a
+    factor measured in the call before (upload against rollout time), so
+    successive calls cut the same samples differently; a new stream starts
+    over with doubling.  Every call's statistics and outputs are byte-identical
+    to the first call's."""
+    m = ai.single_model()
+    n = 3_000_001
+    p = aeb.aeb_sample_params(m, ai.single_scenario(seed=44), 0, n)
+    which = ("status", "x_ref", "n_steps")
+    ref_out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in which}
+    s1 = torch.cuda.Stream()
+    ref = bytes(aeb.aeb_evaluate(m, p, n, aeb.FP32_COMP, aeb.hist_spec(), host_out=ref_out,
+                                 stream=s1))
+    for stream in (s1, s1, s1, torch.cuda.Stream()):
+        out = {k: np.empty(n, dtype=aeb.OUT_DTYPES[k]) for k in which}
+        st = aeb.aeb_evaluate(m, p, n, aeb.FP32_COMP, aeb.hist_spec(), host_out=out,
+                              stream=stream)
+        assert bytes(st) == ref
+        for k in which:
+            assert np.array_equal(out[k].view(np.uint8), ref_out[k].view(np.uint8)), k
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_evaluate_chunked_perception_keys(aeb, precision):
     """Per-step perception readings are keyed by the sample's row in the
