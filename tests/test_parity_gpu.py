@@ -126,6 +126,13 @@ FP64_CASES = {
                             ai.single_scenario(seed=41), 3_000),
     "ttc_perception_all_missing": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=1.0, perc_drop=1.0,
                                               perc_seed=42), ai.single_scenario(seed=42), 2_000),
+    # the serving stream's icy road class (the friction cap binds from onset),
+    # the TTC trigger at a fine step, and the TTC trigger with Eq. 5's cap
+    "icy_road": (ai.single_model(), ai.replace(ai.single_scenario(seed=45),
+                                               mu=ai.uniform(*ai.ROAD_CLASSES["icy"])), 3_000),
+    "ttc_fine_dt_0.1ms": (ai.ttc_model(thr=2.0, dt=1e-4), ai.single_scenario(seed=46), 300),
+    "ttc_lumped": (ai.replace(ai.ttc_model(thr=1.5), cap_mode=ai.CAP_LUMPED),
+                   ai.single_scenario(seed=47), 3_000),
 }
 
 
@@ -210,6 +217,14 @@ FP32_CASES = {
                             ai.single_scenario(seed=43), 10_000),
     "ttc_perception_all_missing": (ai.replace(ai.ttc_model(thr=2.0), perc_sigma=1.0, perc_drop=1.0,
                                               perc_seed=44), ai.single_scenario(seed=44), 5_000),
+    # the serving stream's icy road class (the friction cap binds from onset,
+    # long stops and many contacts), the TTC trigger at a fine step (trigger
+    # tests bounded over many short steps), the TTC trigger with Eq. 5's cap
+    "icy_road": (ai.single_model(), ai.replace(ai.single_scenario(seed=48),
+                                               mu=ai.uniform(*ai.ROAD_CLASSES["icy"])), 10_000),
+    "ttc_fine_dt_0.1ms": (ai.ttc_model(thr=2.0, dt=1e-4), ai.single_scenario(seed=49), 400),
+    "ttc_lumped": (ai.replace(ai.ttc_model(thr=1.5), cap_mode=ai.CAP_LUMPED),
+                   ai.single_scenario(seed=50), 10_000),
 }
 
 
