@@ -63,6 +63,9 @@ FP32_THREAD_INST_PER_STEP = 22.46
 FP32_ISSUE_PEAK = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6  # lane-instructions/s
 
 
+EXTRAS = ("grid", "sweep", "dt", "c1", "lead", "perception", "rare")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -86,8 +89,17 @@ def parse():
     ap.add_argument("--c1-full", action="store_true",
                     help="run the binary64 kernel at every N x dt cell of the N sweep")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched-grid and TTC-sweep lines")
-    return ap.parse_args()
+                    help="skip the extra lines (grid, sweep, dt study, N x dt, moving lead, "
+                         "perception, rare event)")
+    ap.add_argument("--extras", default=",".join(EXTRAS),
+                    help="comma-separated extra lines to run (default: all of "
+                         + ",".join(EXTRAS) + ")")
+    args = ap.parse_args()
+    args.extras = set() if args.no_extras else {e for e in args.extras.split(",") if e}
+    unknown = args.extras - set(EXTRAS)
+    if unknown:
+        ap.error(f"unknown --extras {sorted(unknown)}; choose from {','.join(EXTRAS)}")
+    return args
 
 
 class ClockSampler:
@@ -786,20 +798,23 @@ def main():
     del P, O
     torch.cuda.empty_cache()
     batched = sweep = dts = moving = percep = rare = c1 = None
-    if single and not args.no_extras:
-        batched = batched_run(aeb, torch, dev, stream)
-        torch.cuda.empty_cache()
-        sweep = sweep_run(aeb)
-        torch.cuda.empty_cache()
-        dts = dt_study(aeb, torch)
-        torch.cuda.empty_cache()
-        c1 = c1_sweep(aeb, torch, args.c1_full)
-        torch.cuda.empty_cache()
-        moving = moving_lead_run(aeb, torch)
-        torch.cuda.empty_cache()
-        percep = perception_run(aeb, torch)
-        torch.cuda.empty_cache()
-        rare = rare_event_run(aeb, torch)
+    if single:
+        ex = args.extras
+
+        def run(name, fn):
+            if name not in ex:
+                return None
+            r = fn()
+            torch.cuda.empty_cache()
+            return r
+
+        batched = run("grid", lambda: batched_run(aeb, torch, dev, stream))
+        sweep = run("sweep", lambda: sweep_run(aeb))
+        dts = run("dt", lambda: dt_study(aeb, torch))
+        c1 = run("c1", lambda: c1_sweep(aeb, torch, args.c1_full))
+        moving = run("lead", lambda: moving_lead_run(aeb, torch))
+        percep = run("perception", lambda: perception_run(aeb, torch))
+        rare = run("rare", lambda: rare_event_run(aeb, torch))
 
     clocks = clk.summary()
     line = {
